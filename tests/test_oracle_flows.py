@@ -1,0 +1,255 @@
+"""Closed-form and invariant pins of the full oracle time step (CPU only).
+
+Each steady solution below solves the axisymmetric equations (Eq. 1a-1e)
+exactly; the oracle must converge to it at second order in the grid spacing.
+Together they exercise every geometric source term of Eq. 4, 7 and 9, the
+bounce-back, anti-bounce-back, porous-wall, axis and periodic rules:
+
+* Taylor-Couette (Sec. 3.1): u_theta = A r + B / r            -> S_psi, g walls
+* Hagen-Poiseuille: u_z = G (R^2 - r^2) / (4 mu)              -> F_x^A, axis, body force
+* annular conduction: T = ln(r/R_o) / ln(R_i/R_o), Nu = 1/ln 2 -> S_phi, h walls, Nu
+* cylinder conduction: T = 1 - z/H, Nu = 1 on both end walls   -> end-wall Nu
+* porous rotating cylinders, u_r = Q / r:
+  u_theta = A r^(1+Q/nu) + B/r, T = C r^(Q/alpha) + D,
+  u_z = -G r^2/(2(2 nu - Q)) + E r^(Q/nu) + F                 -> M^A, F^A_y, S_psi, S_phi
+                                                                  with radial flow
+* mass: conserved to round-off without geometric sources; with them the
+  mass budget closes (Eq. 23) and the radius-weighted mass is conserved to
+  truncation error.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_10241_gb300 import workloads as W
+
+
+def run_steady(case, chunk=500, tol=1e-11, max_steps=400_000):
+    o = oracle.Oracle(case.params)
+    o.init_fields(case.fields)
+    prev = o.fields()
+    steps = 0
+    while steps < max_steps:
+        o.step(chunk)
+        steps += chunk
+        cur = o.fields()
+        scale = max(np.max(np.abs(cur[1:4])), 1e-30)
+        if np.max(np.abs(cur[1:4] - prev[1:4])) < tol * scale * chunk / 500 and \
+                np.max(np.abs(cur[4] - prev[4])) < tol * chunk / 500 * 10:
+            return o, cur
+        prev = cur
+    raise AssertionError("no steady state")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def order(errors):
+    return [math.log2(errors[i] / errors[i + 1]) for i in range(len(errors) - 1)]
+
+
+# ---- Taylor-Couette ----------------------------------------------------------
+
+def couette_exact(case, r):
+    p = case.params
+    Ri, Ro = p["r0"], p["r0"] + p["nr"]
+    Oi, Oo = p["omega_i"], p["omega_o"]
+    A = (Oo * Ro**2 - Oi * Ri**2) / (Ro**2 - Ri**2)
+    B = (Oi - Oo) * Ri**2 * Ro**2 / (Ro**2 - Ri**2)
+    return A * r + B / r
+
+
+def test_taylor_couette_second_order():
+    errs = []
+    for Ro in (20, 40, 80):
+        case = W.taylor_couette(R_o=Ro, beta=0.5, kappa=0.1, tau=0.6, Re=5.0)
+        o, fl = run_steady(case)
+        r = W.radii(case.nr, case.params["r0"])
+        errs.append(rel_l2(fl[3, 1], couette_exact(case, r)))
+        # no meridian flow develops
+        assert np.max(np.abs(fl[1:3])) < 1e-3 * np.max(np.abs(fl[3]))
+    p = order(errs)
+    assert errs[-1] < 2e-3, errs
+    assert min(p) > 1.7, (errs, p)
+
+
+def test_taylor_couette_paper_radius_ratios():
+    """Sec. 3.1 parameters (kappa = 0.1, tau = 0.6, Re = 5) at R_o = 50."""
+    for beta in (0.103, 0.203, 0.303, 0.503):
+        case = W.taylor_couette(R_o=50, beta=beta, kappa=0.1, tau=0.6, Re=5.0)
+        o, fl = run_steady(case)
+        r = W.radii(case.nr, case.params["r0"])
+        # the walls sit at the rounded gap: compare with the closed form there
+        assert rel_l2(fl[3, 1], couette_exact(case, r)) < 5e-3, beta
+
+
+def test_couette_radial_pressure_balance():
+    """Radial momentum (Eq. 1b at rest): d p / d r = rho u_theta^2 / r with
+    p = c^2 rho; checks the sign and size of the psi^2/(rho y) term in F_y^A."""
+    case = W.taylor_couette(R_o=40, beta=0.5, kappa=2.0, tau=0.8, Re=40.0)
+    o, fl = run_steady(case, tol=1e-12)
+    r = W.radii(case.nr, case.params["r0"])
+    rho, ut = fl[0, 1], fl[3, 1]
+    dpdr = (rho[2:] - rho[:-2]) / 2.0 / 3.0
+    want = rho[1:-1] * ut[1:-1] ** 2 / r[1:-1]
+    assert rel_l2(dpdr, want) < 0.05
+
+
+# ---- Hagen-Poiseuille --------------------------------------------------------
+
+def test_hagen_poiseuille_second_order():
+    errs = []
+    for R in (8, 16, 32):
+        G = 1e-4 / R**2
+        case = W.hagen_poiseuille(R=R, G=G, tau=0.8)
+        o, fl = run_steady(case, tol=1e-12)
+        r = W.radii(R, 0.0)
+        mu = case.params["nu"] * case.params["rho0"]
+        exact = G * (R * R - r * r) / (4 * mu)
+        errs.append(rel_l2(fl[1, 1], exact))
+        assert np.max(np.abs(fl[2])) < 1e-6 * np.max(exact)
+    p = order(errs)
+    assert errs[-1] < 2e-3, errs
+    assert min(p) > 1.7, (errs, p)
+
+
+# ---- conduction ---------------------------------------------------------------
+
+def test_annular_conduction_profile_and_nusselt():
+    """The profile converges at second order; the Nusselt numbers, one-sided
+    wall derivatives of a second-order field, converge at first order."""
+    errs, nus = [], []
+    for nr in (8, 16, 32, 64):
+        case = W.annular_conduction(nr=nr, ratio=2.0, alpha=0.1)
+        o, fl = run_steady(case, tol=1e-13)
+        Ri = case.params["r0"]
+        Ro = Ri + nr
+        r = W.radii(nr, Ri)
+        exact = np.log(r / Ro) / np.log(Ri / Ro)
+        errs.append(rel_l2(fl[4, 1], exact))
+        d = o.diag()
+        nus.append((d["nu_i"], d["nu_o"]))
+    p = order(errs)
+    assert min(p) > 1.7, (errs, p)
+    nu_exact = 1.0 / math.log(2.0)
+    ni, no = nus[-1]
+    assert ni == pytest.approx(nu_exact, rel=5e-3)
+    assert no == pytest.approx(nu_exact, rel=5e-3)
+    for side in (0, 1):
+        e_nu = [abs(v[side] - nu_exact) for v in nus]
+        assert min(order(e_nu)) > 0.8, e_nu
+
+
+def test_cylinder_conduction_linear_profile_and_unit_nusselt():
+    case = W.cylinder_conduction(nr=8, nz=16, alpha=0.1)
+    o, fl = run_steady(case, tol=1e-14)
+    x = np.arange(16) + 0.5
+    exact = 1.0 - x / 16.0
+    assert np.max(np.abs(fl[4] - exact[:, None])) < 1e-10
+    d = o.diag()
+    assert d["nu_side"][0] == pytest.approx(1.0, abs=1e-9)
+    assert d["nu_side"][1] == pytest.approx(1.0, abs=1e-9)
+    assert d["nu_avg"] == pytest.approx(1.0, abs=1e-9)
+
+
+# ---- radial throughflow between porous rotating cylinders ---------------------
+
+def porous_exact(case, r, G):
+    p = case.params
+    Ri, Ro = p["r0"], p["r0"] + p["nr"]
+    Q = p["sides"][2]["u_wy"] * Ri
+    nu, al = p["nu"], p["alpha"]
+    q, pe = Q / nu, Q / al
+    # u_theta = A r^(1+q) + B / r
+    ui, uo = p["sides"][2]["omega"] * Ri, p["sides"][3]["omega"] * Ro
+    M = np.array([[Ri ** (1 + q), 1 / Ri], [Ro ** (1 + q), 1 / Ro]])
+    A, B = np.linalg.solve(M, [ui, uo])
+    ut = A * r ** (1 + q) + B / r
+    # T = C r^pe + D
+    Ti, To = p["sides"][2]["T_w"], p["sides"][3]["T_w"]
+    Cc, Dd = np.linalg.solve(np.array([[Ri**pe, 1.0], [Ro**pe, 1.0]]), [Ti, To])
+    T = Cc * r**pe + Dd
+    # u_z = a r^2 / 2 + E r^q + F with a = -G / (2 nu - Q)
+    a = -G / (2 * nu - Q)
+    E, F = np.linalg.solve(np.array([[Ri**q, 1.0], [Ro**q, 1.0]]),
+                           [-a * Ri**2 / 2, -a * Ro**2 / 2])
+    uz = a * r**2 / 2 + E * r**q + F
+    return Q / r, ut, T, uz
+
+
+def test_porous_annulus_second_order():
+    errs = {"ur": [], "ut": [], "T": [], "uz": []}
+    for nr in (8, 16, 32):
+        G = 2e-5 * (8.0 / nr) ** 2
+        case = W.porous_annulus(nr=nr, ratio=2.0, Q=0.02, nu=0.1, alpha=0.1,
+                                u_theta_in=1e-3, G=G)
+        o, fl = run_steady(case, tol=1e-12)
+        r = W.radii(nr, case.params["r0"])
+        ur, ut, T, uz = porous_exact(case, r, G)
+        errs["ur"].append(rel_l2(fl[2, 1], ur))
+        errs["ut"].append(rel_l2(fl[3, 1], ut))
+        errs["T"].append(rel_l2(fl[4, 1], T))
+        errs["uz"].append(rel_l2(fl[1, 1], uz))
+    for k, e in errs.items():
+        p = order(e)
+        assert e[-1] < 5e-3, (k, e)
+        assert min(p) > 1.6, (k, e, p)
+
+
+# ---- mass ---------------------------------------------------------------------
+
+def _convecting_box(planar):
+    case = W.annulus_convection(nr=12, nz=16, ratio=2.0, Ra=1e4, Pr=0.7, amp=1e-3, seed=3,
+                                swirl_inner=0.02)
+    p = dict(case.params)
+    p["planar"] = 1 if planar else 0
+    return W.Case("box", p, case.fields)
+
+
+def test_mass_conserved_without_geometric_sources():
+    c = _convecting_box(planar=True)
+    o = oracle.Oracle(c.params)
+    o.init_fields(c.fields)
+    m0 = o.diag()["mass"]
+    o.step(400)
+    d = o.diag()
+    assert d["u_max"] > 1e-5  # there is a flow
+    assert abs(d["mass"] - m0) < 1e-12 * m0
+
+
+def test_mass_budget_closes_with_geometric_source():
+    """Eq. 23: the zeroth moment of f changes in one step by exactly the mass
+    source M^A = -rho u_y / y (Eq. 4a) of that step's pre-collision state."""
+    c = _convecting_box(planar=False)
+    o = oracle.Oracle(c.params)
+    o.init_fields(c.fields)
+    o.step(200)
+    y = W.radii(c.nr, c.params["r0"])[None, :]
+    for _ in range(3):
+        m0 = o.diag()["mass"]
+        o.step(1)
+        fl = o.fields()
+        MA = float(np.sum(-fl[0] * fl[2] / y))
+        m1 = o.diag()["mass"]
+        assert abs(m1 - m0 - MA) < 1e-12 * m0
+        assert abs(MA) > 1e-9
+
+
+def test_radius_weighted_mass_conserved_to_truncation():
+    """The 3-D mass sum(rho y) changes only at truncation order; a sign error in
+    M^A would change it by about 2 sum|rho u_y| per step."""
+    c = _convecting_box(planar=False)
+    o = oracle.Oracle(c.params)
+    o.init_fields(c.fields)
+    d0 = o.diag()
+    flux = 0.0
+    for _ in range(20):
+        o.step(50)
+        fl = o.fields()
+        flux += 50 * float(np.sum(np.abs(fl[0] * fl[2])))
+    d1 = o.diag()
+    assert flux > 0
+    assert abs(d1["mass_r"] - d0["mass_r"]) < 0.02 * flux

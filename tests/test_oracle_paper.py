@@ -1,0 +1,53 @@
+"""Pins of the coupled oracle against numbers printed in the paper (CPU only).
+
+Table 1 (Sec. 3.2) gives the mean Nusselt number of natural convection in a
+vertical annulus computed on a 200 x 200 grid.  The oracle runs the same
+problem on much coarser grids, so the pin is loose (about 1 %); the values
+converge towards the table as the grid is refined.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_10241_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1_nusselt.txt")
+
+
+def table1():
+    rows = [l.split() for l in open(GOLDEN) if l.strip() and not l.startswith("#")]
+    return {float(a): float(b) for a, b in rows}
+
+
+def run_to_steady_nu(case, chunk=1000, tol=1e-7, max_steps=300_000):
+    o = oracle.Oracle(case.params)
+    o.init_fields(case.fields)
+    prev = None
+    for _ in range(max_steps // chunk):
+        o.step(chunk)
+        d = o.diag()
+        if prev is not None and abs(d["nu_avg"] - prev) < tol:
+            return d
+        prev = d["nu_avg"]
+    raise AssertionError("no steady state")
+
+
+@pytest.mark.parametrize("Ra,L,rel", [(1e3, 24, 5e-3), (1e4, 24, 1.2e-2), (1e5, 32, 1.2e-2)])
+def test_annulus_mean_nusselt_matches_table1(Ra, L, rel):
+    nu_paper = table1()[Ra]
+    case = W.annulus_convection(nr=L, nz=2 * L, ratio=2.0, Ra=Ra, Pr=0.7, amp=0.0)
+    d = run_to_steady_nu(case)
+    assert d["nu_avg"] == pytest.approx(nu_paper, rel=rel)
+    # energy balance: the heat entering at the inner wall leaves at the outer
+    assert d["nu_i"] == pytest.approx(d["nu_o"], rel=0.03)
+
+
+def test_annulus_nusselt_converges_towards_table1():
+    nu_paper = table1()[1e3]
+    errs = []
+    for L in (12, 24):
+        case = W.annulus_convection(nr=L, nz=2 * L, ratio=2.0, Ra=1e3, Pr=0.7, amp=0.0)
+        errs.append(abs(run_to_steady_nu(case)["nu_avg"] - nu_paper))
+    assert errs[1] < errs[0]
