@@ -167,11 +167,11 @@ class Oracle:
         lib().orc_init_fields(self._h, _dp(a))
 
     def set_dist(self, d: np.ndarray) -> None:
-        a = np.ascontiguousarray(d, dtype=np.float64).reshape(23, self.nz, self.nr)
+        a = np.ascontiguousarray(d, dtype=np.float64).reshape(19, self.nz, self.nr)
         lib().orc_set_dist(self._h, _dp(a))
 
     def get_dist(self) -> np.ndarray:
-        a = np.empty((23, self.nz, self.nr), np.float64)
+        a = np.empty((19, self.nz, self.nr), np.float64)
         lib().orc_get_dist(self._h, _dp(a))
         return a
 
@@ -179,8 +179,8 @@ class Oracle:
         lib().orc_step(self._h, int(n))
 
     def fields(self) -> np.ndarray:
-        """[5, nz, nr]: rho, u_x (axial), u_y (radial), u_theta, T of the last
-        pre-collision state."""
+        """[5, nz, nr]: rho, u_x (axial), u_y (radial), u_theta, T of the
+        pre-collision state the next step would collide."""
         a = np.empty((5, self.nz, self.nr), np.float64)
         lib().orc_fields(self._h, _dp(a))
         return a

@@ -169,15 +169,15 @@ void orc_post_d2q5(const double g[5], const double q[5], double gp[5])
 
 /* ---- state ------------------------------------------------------------ */
 
-/* The state of a lattice between steps: the post-collision distributions
- * and the macroscopic fields of the last pre-collision state (u_x, u_y,
- * u_theta, T), from which the next step takes its gradients. */
+/* The state of a lattice between steps is its post-collision
+ * distributions.  G holds, during a step, the macroscopic fields of that
+ * stored state (pass 0); Gn receives the pre-collision fields (pass 2). */
 struct orc_state {
     orc_params p;
     size_t n;                 /* nodes                                   */
     double *f, *g, *h;        /* stored post-collision distributions     */
-    double *G;                /* [4][n] gradient fields u_x, u_y, u_theta, T */
-    double *Gn;               /* [4][n] fields written by the current step */
+    double *G;                /* [4][n] u_x, u_y, u_theta, T of the stored state */
+    double *Gn;               /* [5][n] pre-collision rho, u_x, u_y, u_theta, T */
     double *fs, *gs, *hs;     /* streamed distributions (pass 1)         */
     double *rho, *ux, *uy, *psi, *phi; /* output moments (pass 1)        */
     int64_t step;
@@ -223,7 +223,7 @@ orc_state *orc_create(const orc_params *p)
     s->g = (double *)calloc(s->n * 5, sizeof(double));
     s->h = (double *)calloc(s->n * 5, sizeof(double));
     s->G = (double *)calloc(s->n * 4, sizeof(double));
-    s->Gn = (double *)calloc(s->n * 4, sizeof(double));
+    s->Gn = (double *)calloc(s->n * 5, sizeof(double));
     s->fs = (double *)calloc(s->n * 9, sizeof(double));
     s->gs = (double *)calloc(s->n * 5, sizeof(double));
     s->hs = (double *)calloc(s->n * 5, sizeof(double));
@@ -242,7 +242,6 @@ orc_state *orc_create(const orc_params *p)
         orc_eq_d2q9(p->rho0, 0.0, 0.0, s->f + 9 * k);
         orc_eq_d2q5(0.0, 0.0, 0.0, s->g + 5 * k);
         orc_eq_d2q5(p->T0, 0.0, 0.0, s->h + 5 * k);
-        s->G[3 * s->n + k] = p->T0;
     }
     return s;
 }
@@ -285,10 +284,6 @@ int orc_init_fields(orc_state *s, const double *fields)
         orc_eq_d2q9(rho, ux, uy, s->f + 9 * k);
         orc_eq_d2q5(rho * ut, ux, uy, s->g + 5 * k);
         orc_eq_d2q5(T, ux, uy, s->h + 5 * k);
-        s->G[k] = ux;
-        s->G[n + k] = uy;
-        s->G[2 * n + k] = ut;
-        s->G[3 * n + k] = T;
     }
     s->step = 0;
     return 0;
@@ -301,7 +296,6 @@ int orc_set_dist(orc_state *s, const double *d)
         for (int a = 0; a < 9; ++a) s->f[9 * k + a] = d[(size_t)a * n + k];
         for (int a = 0; a < 5; ++a) s->g[5 * k + a] = d[(size_t)(9 + a) * n + k];
         for (int a = 0; a < 5; ++a) s->h[5 * k + a] = d[(size_t)(14 + a) * n + k];
-        for (int q = 0; q < 4; ++q) s->G[(size_t)q * n + k] = d[(size_t)(19 + q) * n + k];
     }
     return 0;
 }
@@ -313,9 +307,36 @@ int orc_get_dist(const orc_state *s, double *d)
         for (int a = 0; a < 9; ++a) d[(size_t)a * n + k] = s->f[9 * k + a];
         for (int a = 0; a < 5; ++a) d[(size_t)(9 + a) * n + k] = s->g[5 * k + a];
         for (int a = 0; a < 5; ++a) d[(size_t)(14 + a) * n + k] = s->h[5 * k + a];
-        for (int q = 0; q < 4; ++q) d[(size_t)(19 + q) * n + k] = s->G[(size_t)q * n + k];
     }
     return 0;
+}
+
+/* ---- pass 0: macroscopic fields of the stored state ------------------- */
+
+/* u_x, u_y, u_theta = psi / rho and T of the stored post-collision
+ * distributions: the fields of the previous time level, whose central
+ * differences enter the sources of this step. */
+static void pass0(orc_state *s)
+{
+    const size_t n = s->n;
+#pragma omp parallel for schedule(static)
+    for (long kk = 0; kk < (long)n; ++kk) {
+        const size_t k = (size_t)kk;
+        double rho = 0, jx = 0, jy = 0, psi = 0, phi = 0;
+        for (int a = 0; a < 9; ++a) {
+            rho += s->f[9 * k + a];
+            jx += s->f[9 * k + a] * EX9[a];
+            jy += s->f[9 * k + a] * EY9[a];
+        }
+        for (int a = 0; a < 5; ++a) {
+            psi += s->g[5 * k + a];
+            phi += s->h[5 * k + a];
+        }
+        s->G[k] = jx / rho;
+        s->G[n + k] = jy / rho;
+        s->G[2 * n + k] = psi / rho;
+        s->G[3 * n + k] = phi;
+    }
 }
 
 /* ---- pass 1: streaming with boundary rules ---------------------------- */
@@ -425,7 +446,7 @@ static void pass1(orc_state *s)
 /* ---- pass 2: gradients, sources, collisions --------------------------- */
 
 /* Neighbour values for the central differences of the gradient fields
- * (the macroscopic fields of the previous step).  Across a half-way wall
+ * (the macroscopic fields of the stored, previous-step state).  Across a half-way wall
  * the ghost value is the linear extrapolation through the wall value
  * (2 q_w - q_1); across a zero-flux wall it is q_1; across the axis u_x, T
  * are even and u_y, u_theta are odd; a periodic side wraps. */
@@ -470,7 +491,7 @@ static double uy_x_neighbour(const orc_state *s, int i, int j, int di)
     return 2.0 * p->side[side].u_wy - Uy[NODE(s, i, j)];
 }
 
-static void pass2(orc_state *s)
+static void pass2(orc_state *s, int write)
 {
     const orc_params *p = &s->p;
     double om9[9], om5s[5], om5t[5];
@@ -491,7 +512,7 @@ static void pass2(orc_state *s)
             const double rho_o = s->rho[k], ux_o = s->ux[k], uy_o = s->uy[k];
             const double psi_o = s->psi[k], phi_o = s->phi[k];
 
-            /* central differences of the previous step's macroscopic fields */
+            /* central differences of the previous time level's fields */
             const nb_t up = j + 1 < p->nr ? node_vals(s, i, j + 1) : ghost_y(s, i, j, 3);
             const nb_t dn = j - 1 >= 0 ? node_vals(s, i, j - 1) : ghost_y(s, i, j, 2);
             const double dyux = 0.5 * (up.ux - dn.ux);
@@ -540,11 +561,14 @@ static void pass2(orc_state *s)
             }
             const double rho = st[0], ux = st[1] / rho, uy = st[2] / rho;
             const double psi = st[3], phi = st[4];
-            /* the pre-collision fields are the next step's gradient fields */
-            s->Gn[k] = ux;
-            s->Gn[s->n + k] = uy;
-            s->Gn[2 * s->n + k] = psi / rho;
-            s->Gn[3 * s->n + k] = phi;
+            if (!write) {
+                s->Gn[k] = rho;
+                s->Gn[s->n + k] = ux;
+                s->Gn[2 * s->n + k] = uy;
+                s->Gn[3 * s->n + k] = psi / rho;
+                s->Gn[4 * s->n + k] = phi;
+                continue;
+            }
 
             /* cascaded collisions, Eq. 17, 34, 49; source moments Eq. 26, 41, 51 */
             double ph[9], qh[5], rh[5];
@@ -568,38 +592,29 @@ static void pass2(orc_state *s)
 int orc_step(orc_state *s, int nsteps)
 {
     for (int t = 0; t < nsteps; ++t) {
+        pass0(s);
         pass1(s);
-        pass2(s);
-        double *t = s->G;
-        s->G = s->Gn;
-        s->Gn = t;
+        pass2(s, 1);
         s->step += 1;
     }
     return 0;
 }
 
-/* Macroscopic fields of the last pre-collision state: u_x, u_y, u_theta, T
- * are the stored gradient fields; rho follows from the stored distribution,
- * whose zeroth moment is rho^o + M^A = rho + M^A / 2 with M^A = -rho u_y / y
- * (Eq. 21a, 23), so rho = sum f / (1 - u_y / (2 y)). */
-static double node_rho(const orc_state *s, size_t k, int j)
+/* Macroscopic fields of the current state: the pre-collision state
+ * (rho, u, u_theta = psi / rho, T after the source half steps) that the
+ * next step's collision would use.  Runs passes 0-2 without writing. */
+static void precollision_fields(const orc_state *cs)
 {
-    double m = 0;
-    for (int a = 0; a < 9; ++a) m += s->f[9 * k + a];
-    if (s->p.planar) return m;
-    const double y = s->p.r0 + j + 0.5;
-    return m / (1.0 - s->G[s->n + k] / (2.0 * y));
+    orc_state *s = (orc_state *)cs; /* touches scratch arrays only */
+    pass0(s);
+    pass1(s);
+    pass2(s, 0);
 }
 
 int orc_fields(const orc_state *s, double *fields)
 {
-    const size_t n = s->n;
-    for (int i = 0; i < s->p.nz; ++i)
-        for (int j = 0; j < s->p.nr; ++j) {
-            const size_t k = NODE(s, i, j);
-            fields[k] = node_rho(s, k, j);
-            for (int q = 0; q < 4; ++q) fields[(size_t)(q + 1) * n + k] = s->G[(size_t)q * n + k];
-        }
+    precollision_fields(s);
+    memcpy(fields, s->Gn, 5 * s->n * sizeof(double));
     return 0;
 }
 
@@ -614,7 +629,8 @@ int orc_fields(const orc_state *s, double *fields)
 int orc_diag_compute(const orc_state *s, orc_diag *out)
 {
     const orc_params *p = &s->p;
-    const double *Tf = s->G + 3 * s->n;
+    precollision_fields(s);
+    const double *Tf = s->Gn + 4 * s->n;
     memset(out, 0, sizeof(*out));
     const int nr = p->nr, nz = p->nz;
     const double H = nz, Ri = p->r0, Ro = p->r0 + nr;
@@ -685,7 +701,7 @@ int orc_diag_compute(const orc_state *s, orc_diag *out)
             mass += m;
             mass_r += m * y;
             tsum += Tf[k];
-            const double ux = s->G[k], uy = s->G[s->n + k];
+            const double ux = s->Gn[s->n + k], uy = s->Gn[2 * s->n + k];
             const double um = sqrt(ux * ux + uy * uy);
             if (um > umax) umax = um;
         }

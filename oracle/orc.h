@@ -14,9 +14,7 @@
  *           (Eq. 21, 38, 48), cascaded collisions (Eq. 17, 34, 49), source
  *           moments (Eq. 26, 41, 51), back-transforms (Eq. 27, 42, 52).
  * Distributions are stored as absolute FP64 values, array-of-structures
- * per node (f[9], g[5], h[5]), node index = z * nr + r.  The state also
- * holds the macroscopic fields (u_x, u_y, u_theta, T) of the last
- * pre-collision state: the gradients of the next step are taken from them.
+ * per node (f[9], g[5], h[5]), node index = z * nr + r.
  *
  * Readings of the paper where it is silent or garbled (listed in the design doc):
  *   - Eq. 34 and 49 print "+(ux^2+uy^2)psi" and "+(ux^2-uy^2)psi"; with that
@@ -26,9 +24,10 @@
  *     "2 c^2 psi" like Eq. 49.
  *   - Sources are evaluated at the pre-collision state of Eq. 21/38/48 (the
  *     state the collision uses), solved by two local sweeps; mu = rho nu.
- *   - Gradients: second-order central differences of the previous step's
- *     pre-collision fields, with ghost values at half-way walls and the axis
- *     (same-step fields make the staggered momentum mode grow in annuli).
+ *   - Gradients: second-order central differences of the macroscopic
+ *     fields of the stored (previous time level) distributions, with ghost
+ *     values at half-way walls and the axis (same-step fields make the
+ *     staggered momentum mode grow in annuli).
  *   - Walls sit half a cell outside the first node: y_j = r0 + j + 1/2,
  *     x_i = i + 1/2.
  *
@@ -95,13 +94,12 @@ int orc_get_threads(void);
 /* initialise every node to the equilibria of the given fields
  * fields: [5][nz][nr] = rho, u_x (axial), u_y (radial), u_theta, T */
 int orc_init_fields(orc_state *s, const double *fields);
-/* canonical state exchange: [23][nz][nr], f0..f8, g0..g4, h0..h4, then the
- * gradient fields u_x, u_y, u_theta, T */
+/* canonical state exchange: [19][nz][nr], f0..f8, g0..g4, h0..h4 */
 int orc_set_dist(orc_state *s, const double *d);
 int orc_get_dist(const orc_state *s, double *d);
 int orc_step(orc_state *s, int nsteps);
-/* fields of the last pre-collision state: [5][nz][nr] rho, u_x, u_y,
- * u_theta, T */
+/* fields of the current state: the pre-collision state the next step's
+ * collision uses, [5][nz][nr] rho, u_x, u_y, u_theta, T */
 int orc_fields(const orc_state *s, double *fields);
 int orc_diag_compute(const orc_state *s, orc_diag *out);
 int64_t orc_get_step(const orc_state *s);
