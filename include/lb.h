@@ -1,0 +1,198 @@
+/*
+ * lb.h -- C ABI of the GB300 axisymmetric thermal cascaded lattice Boltzmann
+ * library (liblbaxi.so).
+ *
+ * The library advances the three distribution functions of the axisymmetric
+ * cascaded central-moment LB method of Hajabdollahi, Premnath & Welch
+ * (arXiv 1806.10241) on the meridian (r, z) plane: D2Q9 f for density and
+ * axial / radial momentum (Sec. 2.2), D2Q5 g for psi = rho u_theta (Sec. 2.3)
+ * and D2Q5 h for the temperature (Sec. 2.4).  Every time step is one fused
+ * CUDA kernel: pull streaming with the wall / axis / periodic rules
+ * (Eq. 16b, 33b, 46b; Sec. 3), the geometric and body-force sources
+ * (Eq. 4a-4c, 5, 7, 9), the pre-collision half steps (Eq. 21, 38, 48), the
+ * cascaded collisions (Eq. 17, 34, 49), the source moments (Eq. 26, 41, 51)
+ * and the back-transforms (Eq. 27, 42, 52).
+ *
+ * Coordinates follow Eq. 2: x = z (axial, rows, index i in [0, nz)),
+ * y = r (radial, columns, index j in [0, nr)).  Walls sit half a cell outside
+ * the first and last nodes: node (i, j) is at x = i + 1/2, y = r_inner + j +
+ * 1/2.  Lattice units: dx = dt = 1, c_s^2 = 1/3.
+ *
+ * Memory ownership: the caller allocates one device buffer of
+ * lb_required_bytes() bytes (256-byte aligned) and one CUDA stream and hands
+ * both to lb_create(); the library never allocates device memory and never
+ * frees the caller's buffer.  All kernels and copies run on that stream.
+ *
+ * Errors: every call returns an lb_status and never aborts, traps or exits;
+ * lb_last_error() gives a one-line description of the last failure of a
+ * context.  A context is not thread safe; distinct contexts on distinct
+ * streams are independent.
+ *
+ * Arrays exchanged with the host are row-major [plane][nz][nr] doubles.
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LB_EXPORT __attribute__((visibility("default")))
+#else
+#define LB_EXPORT
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_ARG = 1,      /* invalid argument or parameter combination      */
+    LB_ERR_NOMEM = 2,    /* the caller's buffer is too small                */
+    LB_ERR_CUDA = 3,     /* a CUDA runtime call failed                      */
+    LB_ERR_DIVERGED = 4, /* non-finite or out-of-range state (diagnostics)  */
+    LB_ERR_TIMEOUT = 5,  /* a bounded device-side wait ran out              */
+    LB_ERR_STATE = 6     /* call out of order (e.g. step before params)     */
+} lb_status;
+
+/* Storage type of the distributions.  LB_FP64 computes in FP64; the other
+ * three compute in FP32.  LB_BF16 / LB_FP16 store deviations from the rest
+ * state (w_a rho0 for f, w_a T0 for h) in 16 bits. */
+typedef enum { LB_FP64 = 0, LB_FP32 = 1, LB_BF16 = 2, LB_FP16 = 3 } lb_storage;
+
+/* Lattice shape.  nr, nz >= 2.  r_inner = 0 puts the axis of symmetry on
+ * the inner side (a cylinder); r_inner > 0 makes an annulus. */
+typedef struct {
+    int32_t nr;        /* radial nodes (columns)                           */
+    int32_t nz;        /* axial nodes (rows)                               */
+    double r_inner;    /* radius of the inner wall (0: axis)               */
+    int32_t storage;   /* lb_storage                                       */
+    int32_t reserved;  /* must be 0                                        */
+} lb_grid_desc;
+
+/* Boundary sides */
+enum { LB_SIDE_BOTTOM = 0, LB_SIDE_TOP = 1, LB_SIDE_INNER = 2, LB_SIDE_OUTER = 3 };
+
+/* Flow (f) boundary types.
+ * LB_FLOW_WALL: half-way bounce-back (Sec. 3.2) with the moving-wall
+ *   momentum term 2 w_a rho0 (e_a . u_w) / c_s^2 for a wall velocity
+ *   u_w = (u_wx, u_wy); u_w = 0 is the no-slip wall, a tangential u_w a
+ *   sliding wall, a normal u_w a porous wall.
+ * LB_FLOW_AXIS: the symmetry line r = 0, mirror rule for the particle
+ *   distributions (Sec. 3.3); only on the inner side with r_inner = 0.
+ * LB_FLOW_PERIODIC: periodic along z (Sec. 3.1); bottom and top together. */
+enum { LB_FLOW_WALL = 0, LB_FLOW_AXIS = 1, LB_FLOW_PERIODIC = 2 };
+
+/* Scalar (g: psi, h: T) boundary types.
+ * LB_SC_DIRICHLET: anti-bounce-back to a wall value (Sec. 3.1, 3.2): for g
+ *   psi_w = rho0 * omega * radius (a rotating wall: the column's radius on an
+ *   end wall, the wall radius on a lateral wall), for h the value T_w.
+ * LB_SC_NEUMANN: zero flux (bounce-back), e.g. an adiabatic wall.
+ * LB_SC_AXIS: symmetry line (psi odd, T even).  LB_SC_PERIODIC: along z. */
+enum { LB_SC_DIRICHLET = 0, LB_SC_NEUMANN = 1, LB_SC_AXIS = 2, LB_SC_PERIODIC = 3 };
+
+typedef struct {
+    int32_t flow;    /* LB_FLOW_*                                          */
+    int32_t swirl;   /* LB_SC_* for g                                      */
+    int32_t heat;    /* LB_SC_* for h                                      */
+    int32_t pad;
+    double u_wx;     /* wall velocity, axial component                     */
+    double u_wy;     /* wall velocity, radial component                    */
+    double omega;    /* wall angular velocity (g Dirichlet)                */
+    double T_w;      /* wall temperature (h Dirichlet)                     */
+} lb_side;
+
+/* Physical parameters in lattice units.
+ *   omega_4 = omega_5 = 1 / (3 nu + 1/2) (shear, Sec. 2.2); omega_3 the bulk
+ *   rate; omega_6..8 = omega_hi; D2Q5: omega_1,2 = 1 / (3 nu + 1/2) for g and
+ *   1 / (3 alpha + 1/2) for h, omega_3,4 = omega_hi (Sec. 2.3, 2.4).
+ *   Body force F_x^b = rho0 g_beta (T - T0) + body_fx (buoyancy, Sec. 3.2).
+ *   planar = 1 switches off every geometric (1/r) source: plain 2-D flow.
+ *   explicit_sources = 1 evaluates the sources once at the post-streaming
+ *   state (the literal reading; see the readings of the paper).  The default
+ *   evaluates them at the pre-collision state by two local sweeps.
+ *   sign_literal = 1 uses the sign printed in Eq. 34 / 49. */
+typedef struct {
+    double nu, alpha, omega3, omega_hi, g_beta, T0, body_fx, rho0;
+    int32_t planar;
+    int32_t sign_literal;
+    int32_t explicit_sources;
+    int32_t pad;
+    lb_side side[4];
+} lb_params;
+
+/* Diagnostics (Sec. 3.2): Nusselt number on each Dirichlet-T side
+ * (lateral wall of radius R_w: -R_w / (H dT) sum dT/dr; end wall:
+ * -(H / dT) (2 / (R_o^2 - R_i^2)) sum dT/dz r), the mean of the two
+ * opposite heated sides, total mass (sum of f), radius-weighted mass, sum
+ * of T and max |u| in the meridian plane -- all accumulated in FP64 from the
+ * pre-collision fields of the current state. */
+typedef struct {
+    double nu_side[4];
+    double nu_i, nu_o, nu_avg;
+    double mass, mass_r, T_sum, u_max;
+    int64_t step;
+    int32_t status;  /* LB_OK or LB_ERR_DIVERGED                          */
+    int32_t pad;
+} lb_diag;
+
+/* Bytes of device memory a lattice of this shape needs (2 distribution
+ * buffers + reduction scratch).  Returns LB_ERR_ARG for an invalid desc. */
+LB_EXPORT lb_status lb_required_bytes(const lb_grid_desc *desc, size_t *bytes);
+
+/* Create a context on the caller's device buffer (>= lb_required_bytes,
+ * 256-byte aligned) and CUDA stream (cudaStream_t as void*, NULL = legacy
+ * default stream).  The lattice is unusable until lb_set_params(). */
+LB_EXPORT lb_status lb_create(const lb_grid_desc *desc, void *dev_buf, size_t bytes, void *cuda_stream,
+                    lb_ctx **out);
+
+/* Set the parameters and reset the state to rest: rho0, u = 0, u_theta = 0,
+ * T = T0, step = 0. */
+LB_EXPORT lb_status lb_set_params(lb_ctx *ctx, const lb_params *params);
+
+/* Initialise every node to the equilibria of host fields [5][nz][nr]:
+ * rho, u_x, u_y, u_theta, T.  step = 0.  Synchronous. */
+LB_EXPORT lb_status lb_init_fields(lb_ctx *ctx, const double *host_fields);
+
+/* Advance nsteps >= 0 time steps, asynchronously on the context's stream. */
+LB_EXPORT lb_status lb_step(lb_ctx *ctx, int32_t nsteps);
+
+/* Pre-collision fields of the current state (the rho, u, u_theta, T the
+ * next collision uses) into host [5][nz][nr] doubles.  Synchronous. */
+LB_EXPORT lb_status lb_get_fields(lb_ctx *ctx, double *host_fields);
+
+/* Diagnostics of the current state.  Synchronous; status LB_ERR_DIVERGED
+ * when a field is not finite or rho leaves [0.5, 1.5]. */
+LB_EXPORT lb_status lb_diagnostics(lb_ctx *ctx, lb_diag *out);
+
+/* Distributions as absolute values, host [19][nz][nr] doubles: f0..f8,
+ * g0..g4, h0..h4 (velocity order of Eq. 10 and Eq. 28).  Synchronous. */
+LB_EXPORT lb_status lb_get_distributions(lb_ctx *ctx, double *host19);
+LB_EXPORT lb_status lb_set_distributions(lb_ctx *ctx, const double *host19);
+
+/* Checkpoint: raw state bytes (lb_state_bytes) plus the step counter. */
+LB_EXPORT lb_status lb_state_bytes(const lb_ctx *ctx, size_t *bytes);
+LB_EXPORT lb_status lb_get_state(lb_ctx *ctx, void *host, size_t bytes);
+LB_EXPORT lb_status lb_set_state(lb_ctx *ctx, const void *host, size_t bytes);
+
+/* Steps taken since the last reset. */
+LB_EXPORT lb_status lb_get_step(const lb_ctx *ctx, int64_t *step);
+
+/* Tune the launch: rows per z-segment of a warp (0 = automatic) and warps
+ * per block (0 = automatic).  Results do not depend on the launch shape. */
+LB_EXPORT lb_status lb_set_launch(lb_ctx *ctx, int32_t seg_rows, int32_t warps_per_block);
+
+/* Release the context (not the caller's buffer or stream). */
+LB_EXPORT lb_status lb_destroy(lb_ctx *ctx);
+
+/* One-line description of the last error on ctx (or of the last failed
+ * lb_create / lb_required_bytes when ctx is NULL).  Never NULL. */
+LB_EXPORT const char *lb_last_error(const lb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LB_H */

@@ -1,0 +1,469 @@
+// Host side of the C ABI declared in include/lb.h.
+//
+// Device memory layout inside the caller's buffer (256-byte aligned parts):
+//   [A: 19 planes][B: 19 planes][partial sums][result]
+// A and B alternate as source and destination of the time steps; the one
+// that is not current doubles as staging space for host exchanges and for
+// the temperature field of the diagnostics.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/lb.h"
+#include "lb_internal.h"
+
+using lbk::HostParams;
+using lbk::Launch;
+
+struct lb_ctx {
+    HostParams hp;
+    bool params_set;
+    char *buf;
+    size_t bytes;
+    size_t dist_bytes;   // one distribution buffer, rounded to 256
+    char *dist[2];
+    double *partial;
+    double *result;
+    cudaStream_t stream;
+    int cur;
+    int64_t step;
+    Launch launch;
+    bool launch_auto;
+    char err[256];
+};
+
+static thread_local char g_err[256] = "";
+
+namespace {
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int pitch_for(int nr, int storage)
+{
+    const int m = lbk::storage_bytes(storage) == 2 ? 64 : 32;
+    return (nr + m - 1) / m * m;
+}
+
+lb_status fail(lb_ctx *ctx, lb_status st, const char *fmt, ...)
+{
+    char *dst = ctx ? ctx->err : g_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+lb_status cuda_fail(lb_ctx *ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, LB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+lb_status check_desc(const lb_grid_desc *d, size_t *plane, size_t *dist_bytes)
+{
+    if (!d) return fail(nullptr, LB_ERR_ARG, "desc is NULL");
+    if (d->nr < 2 || d->nz < 2) return fail(nullptr, LB_ERR_ARG, "nr and nz must be >= 2 (got %d, %d)", d->nr, d->nz);
+    if (d->nr > (1 << 20) || d->nz > (1 << 24)) return fail(nullptr, LB_ERR_ARG, "lattice too large");
+    if (!(d->r_inner >= 0.0) || !std::isfinite(d->r_inner)) return fail(nullptr, LB_ERR_ARG, "r_inner must be >= 0");
+    if (d->storage < LB_FP64 || d->storage > LB_FP16) return fail(nullptr, LB_ERR_ARG, "unknown storage %d", d->storage);
+    if (d->reserved != 0) return fail(nullptr, LB_ERR_ARG, "reserved must be 0");
+    const size_t p = (size_t)d->nz * (size_t)pitch_for(d->nr, d->storage);
+    *plane = p;
+    *dist_bytes = align256(lbk::NQ * p * lbk::storage_bytes(d->storage));
+    return LB_OK;
+}
+
+size_t scratch_bytes() { return align256((size_t)lbk::MAX_DIAG_BLOCKS * lbk::NSUM * sizeof(double)) + 256; }
+
+lb_status validate_params(lb_ctx *ctx, const lb_params *p)
+{
+    const HostParams &h = ctx->hp;
+    if (!(p->nu > 0.0) || !(p->alpha > 0.0) || !(p->rho0 > 0.0))
+        return fail(ctx, LB_ERR_ARG, "nu, alpha and rho0 must be > 0");
+    if (!(p->omega3 > 0.0 && p->omega3 < 2.0) || !(p->omega_hi > 0.0 && p->omega_hi < 2.0))
+        return fail(ctx, LB_ERR_ARG, "omega3 and omega_hi must lie in (0, 2)");
+    const int per0 = p->side[0].flow == LB_FLOW_PERIODIC, per1 = p->side[1].flow == LB_FLOW_PERIODIC;
+    if (per0 != per1) return fail(ctx, LB_ERR_ARG, "periodicity needs both end sides");
+    for (int s = 0; s < 4; ++s) {
+        const lb_side &sd = p->side[s];
+        if (sd.flow < 0 || sd.flow > 2 || sd.swirl < 0 || sd.swirl > 3 || sd.heat < 0 || sd.heat > 3)
+            return fail(ctx, LB_ERR_ARG, "side %d: unknown boundary code", s);
+        const bool per = sd.flow == LB_FLOW_PERIODIC;
+        const bool ax = sd.flow == LB_FLOW_AXIS;
+        if ((sd.swirl == LB_SC_PERIODIC) != per || (sd.heat == LB_SC_PERIODIC) != per)
+            return fail(ctx, LB_ERR_ARG, "side %d: periodic must apply to f, g and h together", s);
+        if ((sd.swirl == LB_SC_AXIS) != ax || (sd.heat == LB_SC_AXIS) != ax)
+            return fail(ctx, LB_ERR_ARG, "side %d: the axis must apply to f, g and h together", s);
+        if (per && s >= 2) return fail(ctx, LB_ERR_ARG, "periodicity only along z");
+        if (ax && (s != 2 || h.r0 != 0.0)) return fail(ctx, LB_ERR_ARG, "the axis is only the inner side of a cylinder");
+        const double vals[4] = {sd.u_wx, sd.u_wy, sd.omega, sd.T_w};
+        for (double v : vals)
+            if (!std::isfinite(v)) return fail(ctx, LB_ERR_ARG, "side %d: non-finite wall value", s);
+    }
+    if (h.r0 == 0.0 && !p->planar && p->side[2].flow != LB_FLOW_AXIS)
+        return fail(ctx, LB_ERR_ARG, "r_inner = 0 needs the axis on the inner side");
+    return LB_OK;
+}
+
+// Rows of `planes` doubles per node that fit in the staging area.
+lb_status staging(lb_ctx *ctx, int planes, double **ptr, int *rows)
+{
+    const size_t per_row = (size_t)planes * ctx->hp.nr * sizeof(double);
+    size_t avail = ctx->dist_bytes;
+    char *base = ctx->dist[1 - ctx->cur];
+    if (avail < per_row) {  // tiny 16-bit lattices: use the reduction scratch
+        avail = (size_t)lbk::MAX_DIAG_BLOCKS * lbk::NSUM * sizeof(double);
+        base = (char *)ctx->partial;
+        if (avail < per_row) return fail(ctx, LB_ERR_NOMEM, "no staging space for one row");
+    }
+    size_t r = avail / per_row;
+    if (r > (size_t)ctx->hp.nz) r = ctx->hp.nz;
+    *ptr = (double *)base;
+    *rows = (int)r;
+    return LB_OK;
+}
+
+lb_status need_params(lb_ctx *ctx)
+{
+    if (!ctx) return fail(nullptr, LB_ERR_ARG, "ctx is NULL");
+    if (!ctx->params_set) return fail(ctx, LB_ERR_STATE, "lb_set_params has not been called");
+    return LB_OK;
+}
+
+Launch diag_launch(const lb_ctx *ctx)
+{
+    Launch l = ctx->launch;
+    const long long nwin = (ctx->hp.nr + 29) / 30;
+    const long long bx = (nwin + 3) / 4;
+    long long segs = (ctx->hp.nz + l.seg_rows - 1) / l.seg_rows;
+    if (bx * segs > lbk::MAX_DIAG_BLOCKS) {
+        segs = lbk::MAX_DIAG_BLOCKS / bx;
+        if (segs < 1) segs = 1;
+        l.seg_rows = (int)((ctx->hp.nz + segs - 1) / segs);
+    }
+    return l;
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_required_bytes(const lb_grid_desc *desc, size_t *bytes)
+{
+    size_t plane, dist;
+    lb_status st = check_desc(desc, &plane, &dist);
+    if (st != LB_OK) return st;
+    if (!bytes) return fail(nullptr, LB_ERR_ARG, "bytes is NULL");
+    *bytes = 2 * dist + scratch_bytes();
+    return LB_OK;
+}
+
+lb_status lb_create(const lb_grid_desc *desc, void *dev_buf, size_t bytes, void *cuda_stream, lb_ctx **out)
+{
+    if (!out) return fail(nullptr, LB_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    size_t plane, dist;
+    lb_status st = check_desc(desc, &plane, &dist);
+    if (st != LB_OK) return st;
+    const size_t need = 2 * dist + scratch_bytes();
+    if (!dev_buf) return fail(nullptr, LB_ERR_ARG, "dev_buf is NULL");
+    if (((uintptr_t)dev_buf & 255) != 0) return fail(nullptr, LB_ERR_ARG, "dev_buf must be 256-byte aligned");
+    if (bytes < need) return fail(nullptr, LB_ERR_NOMEM, "buffer holds %zu bytes, %zu needed", bytes, need);
+    lb_ctx *c = new (std::nothrow) lb_ctx();
+    if (!c) return fail(nullptr, LB_ERR_NOMEM, "host allocation failed");
+    HostParams &h = c->hp;
+    std::memset(&h, 0, sizeof(h));
+    h.nr = desc->nr;
+    h.nz = desc->nz;
+    h.pitch = pitch_for(desc->nr, desc->storage);
+    h.plane = (long long)plane;
+    h.storage = desc->storage;
+    h.r0 = desc->r_inner;
+    h.scale = desc->storage == LB_FP16 ? 1024.0 : 1.0;
+    c->buf = (char *)dev_buf;
+    c->bytes = bytes;
+    c->dist_bytes = dist;
+    c->dist[0] = c->buf;
+    c->dist[1] = c->buf + dist;
+    c->partial = (double *)(c->buf + 2 * dist);
+    c->result = (double *)(c->buf + 2 * dist + align256((size_t)lbk::MAX_DIAG_BLOCKS * lbk::NSUM * sizeof(double)));
+    c->stream = (cudaStream_t)cuda_stream;
+    c->cur = 0;
+    c->step = 0;
+    c->params_set = false;
+    c->launch = lbk::default_launch(h);
+    c->launch_auto = true;
+    c->err[0] = 0;
+    *out = c;
+    return LB_OK;
+}
+
+lb_status lb_set_params(lb_ctx *ctx, const lb_params *p)
+{
+    if (!ctx || !p) return fail(ctx, LB_ERR_ARG, "NULL argument");
+    lb_status st = validate_params(ctx, p);
+    if (st != LB_OK) return st;
+    HostParams &h = ctx->hp;
+    h.nu = p->nu;
+    h.alpha = p->alpha;
+    h.omega3 = p->omega3;
+    h.omega_hi = p->omega_hi;
+    h.g_beta = p->g_beta;
+    h.T0 = p->T0;
+    h.body_fx = p->body_fx;
+    h.rho0 = p->rho0;
+    h.planar = p->planar;
+    h.sign_literal = p->sign_literal;
+    h.explicit_sources = p->explicit_sources;
+    for (int s = 0; s < 4; ++s) {
+        h.flow[s] = p->side[s].flow;
+        h.swirl[s] = p->side[s].swirl;
+        h.heat[s] = p->side[s].heat;
+        h.uwx[s] = p->side[s].u_wx;
+        h.uwy[s] = p->side[s].u_wy;
+        h.omega[s] = p->side[s].omega;
+        h.Tw[s] = p->side[s].T_w;
+    }
+    // rest state: every stored deviation is zero
+    cudaError_t e = cudaMemsetAsync(ctx->dist[0], 0, ctx->dist_bytes, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reset");
+    ctx->cur = 0;
+    ctx->step = 0;
+    ctx->params_set = true;
+    return LB_OK;
+}
+
+lb_status lb_init_fields(lb_ctx *ctx, const double *host_fields)
+{
+    lb_status st = need_params(ctx);
+    if (st != LB_OK) return st;
+    if (!host_fields) return fail(ctx, LB_ERR_ARG, "host_fields is NULL");
+    double *stage;
+    int rows;
+    if ((st = staging(ctx, 5, &stage, &rows)) != LB_OK) return st;
+    const int nr = ctx->hp.nr, nz = ctx->hp.nz;
+    const size_t N = (size_t)nr * nz;
+    for (int r0 = 0; r0 < nz; r0 += rows) {
+        const int r1 = r0 + rows < nz ? r0 + rows : nz;
+        const size_t n = (size_t)(r1 - r0) * nr;
+        for (int q = 0; q < 5; ++q) {
+            cudaError_t e = cudaMemcpyAsync(stage + q * n, host_fields + q * N + (size_t)r0 * nr, n * sizeof(double),
+                                            cudaMemcpyHostToDevice, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "init upload");
+        }
+        cudaError_t e = lbk::launch_init_fields(ctx->hp, stage, ctx->dist[ctx->cur], r0, r1, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "init kernel");
+    }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "init sync");
+    ctx->step = 0;
+    return LB_OK;
+}
+
+lb_status lb_step(lb_ctx *ctx, int32_t nsteps)
+{
+    lb_status st = need_params(ctx);
+    if (st != LB_OK) return st;
+    if (nsteps < 0) return fail(ctx, LB_ERR_ARG, "nsteps < 0");
+    for (int32_t t = 0; t < nsteps; ++t) {
+        cudaError_t e = lbk::launch_step(ctx->hp, ctx->launch, ctx->dist[ctx->cur], ctx->dist[1 - ctx->cur],
+                                         ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
+        ctx->cur ^= 1;
+        ctx->step += 1;
+    }
+    return LB_OK;
+}
+
+lb_status lb_get_fields(lb_ctx *ctx, double *host_fields)
+{
+    lb_status st = need_params(ctx);
+    if (st != LB_OK) return st;
+    if (!host_fields) return fail(ctx, LB_ERR_ARG, "host_fields is NULL");
+    double *stage;
+    int rows;
+    if ((st = staging(ctx, 5, &stage, &rows)) != LB_OK) return st;
+    const int nr = ctx->hp.nr, nz = ctx->hp.nz;
+    const size_t N = (size_t)nr * nz;
+    for (int r0 = 0; r0 < nz; r0 += rows) {
+        const int r1 = r0 + rows < nz ? r0 + rows : nz;
+        const size_t n = (size_t)(r1 - r0) * nr;
+        cudaError_t e = lbk::launch_fields(ctx->hp, ctx->launch, ctx->dist[ctx->cur], stage, r0, r1, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "fields kernel");
+        for (int q = 0; q < 5; ++q) {
+            e = cudaMemcpyAsync(host_fields + q * N + (size_t)r0 * nr, stage + q * n, n * sizeof(double),
+                                cudaMemcpyDeviceToHost, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "fields download");
+        }
+        e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "fields sync");
+    }
+    return LB_OK;
+}
+
+lb_status lb_diagnostics(lb_ctx *ctx, lb_diag *out)
+{
+    lb_status st = need_params(ctx);
+    if (st != LB_OK) return st;
+    if (!out) return fail(ctx, LB_ERR_ARG, "out is NULL");
+    const HostParams &h = ctx->hp;
+    double res[lbk::NSUM];
+    cudaError_t e = lbk::launch_diag(h, diag_launch(ctx), ctx->dist[ctx->cur], ctx->partial,
+                                     (double *)ctx->dist[1 - ctx->cur], ctx->result, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "diagnostics kernel");
+    e = cudaMemcpyAsync(res, ctx->result, sizeof(res), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "diagnostics download");
+    std::memset(out, 0, sizeof(*out));
+    const double N = (double)h.nr * h.nz;
+    const double sum_y = (double)h.nz * (h.nr * h.r0 + 0.5 * (double)h.nr * h.nr);
+    out->mass = h.rho0 * N + res[0];
+    out->mass_r = h.rho0 * sum_y + res[1];
+    out->T_sum = res[2];
+    out->u_max = res[3];
+    for (int s = 0; s < 4; ++s) out->nu_side[s] = res[4 + s];
+    int a = -1, b = -1;
+    if (h.heat[2] == LB_SC_DIRICHLET && h.heat[3] == LB_SC_DIRICHLET) {
+        a = 2;
+        b = 3;
+    } else if (h.heat[0] == LB_SC_DIRICHLET && h.heat[1] == LB_SC_DIRICHLET) {
+        a = 0;
+        b = 1;
+    } else {
+        for (int s = 0; s < 4; ++s)
+            if (h.heat[s] == LB_SC_DIRICHLET) {
+                if (a < 0) a = s;
+                else if (b < 0) b = s;
+            }
+    }
+    if (a >= 0) out->nu_i = out->nu_side[a];
+    if (b >= 0) out->nu_o = out->nu_side[b];
+    out->nu_avg = (a >= 0 && b >= 0) ? 0.5 * (out->nu_i + out->nu_o) : out->nu_i;
+    out->step = ctx->step;
+    const bool bad = res[8] > 0.0 || !std::isfinite(res[0]) || !std::isfinite(res[2]);
+    out->status = bad ? LB_ERR_DIVERGED : LB_OK;
+    return LB_OK;
+}
+
+lb_status lb_get_distributions(lb_ctx *ctx, double *host19)
+{
+    lb_status st = need_params(ctx);
+    if (st != LB_OK) return st;
+    if (!host19) return fail(ctx, LB_ERR_ARG, "host19 is NULL");
+    double *stage;
+    int rows;
+    if ((st = staging(ctx, lbk::NQ, &stage, &rows)) != LB_OK) return st;
+    const int nr = ctx->hp.nr, nz = ctx->hp.nz;
+    const size_t N = (size_t)nr * nz;
+    for (int r0 = 0; r0 < nz; r0 += rows) {
+        const int r1 = r0 + rows < nz ? r0 + rows : nz;
+        const size_t n = (size_t)(r1 - r0) * nr;
+        cudaError_t e = lbk::launch_export(ctx->hp, ctx->dist[ctx->cur], stage, r0, r1, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "export kernel");
+        for (int q = 0; q < lbk::NQ; ++q) {
+            e = cudaMemcpyAsync(host19 + q * N + (size_t)r0 * nr, stage + q * n, n * sizeof(double),
+                                cudaMemcpyDeviceToHost, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "export download");
+        }
+        e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "export sync");
+    }
+    return LB_OK;
+}
+
+lb_status lb_set_distributions(lb_ctx *ctx, const double *host19)
+{
+    lb_status st = need_params(ctx);
+    if (st != LB_OK) return st;
+    if (!host19) return fail(ctx, LB_ERR_ARG, "host19 is NULL");
+    double *stage;
+    int rows;
+    if ((st = staging(ctx, lbk::NQ, &stage, &rows)) != LB_OK) return st;
+    const int nr = ctx->hp.nr, nz = ctx->hp.nz;
+    const size_t N = (size_t)nr * nz;
+    for (int r0 = 0; r0 < nz; r0 += rows) {
+        const int r1 = r0 + rows < nz ? r0 + rows : nz;
+        const size_t n = (size_t)(r1 - r0) * nr;
+        for (int q = 0; q < lbk::NQ; ++q) {
+            cudaError_t e = cudaMemcpyAsync(stage + q * n, host19 + q * N + (size_t)r0 * nr, n * sizeof(double),
+                                            cudaMemcpyHostToDevice, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "import upload");
+        }
+        cudaError_t e = lbk::launch_import(ctx->hp, stage, ctx->dist[ctx->cur], r0, r1, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "import kernel");
+        e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "import sync");
+    }
+    return LB_OK;
+}
+
+lb_status lb_state_bytes(const lb_ctx *ctx, size_t *bytes)
+{
+    if (!ctx || !bytes) return fail(nullptr, LB_ERR_ARG, "NULL argument");
+    *bytes = 16 + ctx->dist_bytes;
+    return LB_OK;
+}
+
+lb_status lb_get_state(lb_ctx *ctx, void *host, size_t bytes)
+{
+    lb_status st = need_params(ctx);
+    if (st != LB_OK) return st;
+    if (!host || bytes < 16 + ctx->dist_bytes) return fail(ctx, LB_ERR_ARG, "state buffer too small");
+    int64_t hdr[2] = {ctx->step, (int64_t)ctx->hp.storage};
+    std::memcpy(host, hdr, 16);
+    cudaError_t e = cudaMemcpyAsync((char *)host + 16, ctx->dist[ctx->cur], ctx->dist_bytes, cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "state download");
+    return LB_OK;
+}
+
+lb_status lb_set_state(lb_ctx *ctx, const void *host, size_t bytes)
+{
+    lb_status st = need_params(ctx);
+    if (st != LB_OK) return st;
+    if (!host || bytes < 16 + ctx->dist_bytes) return fail(ctx, LB_ERR_ARG, "state buffer too small");
+    int64_t hdr[2];
+    std::memcpy(hdr, host, 16);
+    if (hdr[1] != ctx->hp.storage) return fail(ctx, LB_ERR_ARG, "state was saved with another storage type");
+    cudaError_t e = cudaMemcpyAsync(ctx->dist[ctx->cur], (const char *)host + 16, ctx->dist_bytes,
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "state upload");
+    ctx->step = hdr[0];
+    return LB_OK;
+}
+
+lb_status lb_get_step(const lb_ctx *ctx, int64_t *step)
+{
+    if (!ctx || !step) return fail(nullptr, LB_ERR_ARG, "NULL argument");
+    *step = ctx->step;
+    return LB_OK;
+}
+
+lb_status lb_set_launch(lb_ctx *ctx, int32_t seg_rows, int32_t warps_per_block)
+{
+    if (!ctx) return fail(nullptr, LB_ERR_ARG, "ctx is NULL");
+    if (seg_rows < 0 || warps_per_block < 0 || warps_per_block > 8)
+        return fail(ctx, LB_ERR_ARG, "seg_rows >= 0, 0 <= warps_per_block <= 8");
+    Launch d = lbk::default_launch(ctx->hp);
+    ctx->launch.seg_rows = seg_rows ? seg_rows : d.seg_rows;
+    ctx->launch.warps_per_block = warps_per_block ? warps_per_block : d.warps_per_block;
+    ctx->launch_auto = seg_rows == 0 && warps_per_block == 0;
+    return LB_OK;
+}
+
+lb_status lb_destroy(lb_ctx *ctx)
+{
+    delete ctx;
+    return LB_OK;
+}
+
+const char *lb_last_error(const lb_ctx *ctx) { return ctx ? ctx->err : g_err; }
+
+}  // extern "C"

@@ -1,0 +1,60 @@
+// Internal interface between the C ABI (lb_capi.cu) and the kernels
+// (lb_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace lbk {
+
+enum Mode { MODE_STEP = 0, MODE_FIELDS = 1, MODE_DIAG = 2 };
+enum Storage { ST_FP64 = 0, ST_FP32 = 1, ST_BF16 = 2, ST_FP16 = 3 };
+
+constexpr int NQ = 19;        // 9 (f) + 5 (g) + 5 (h) planes
+constexpr int NSUM = 12;      // diagnostic partial sums per block
+constexpr int MAX_DIAG_BLOCKS = 4096;
+
+// Everything a kernel needs about one lattice, in double precision; the
+// launchers convert to the compute type.
+struct HostParams {
+    int nr, nz, pitch;
+    long long plane;          // elements per plane = nz * pitch
+    int storage;
+    double r0;
+    double nu, alpha, omega3, omega_hi, g_beta, T0, body_fx, rho0;
+    int planar, sign_literal, explicit_sources;
+    int flow[4], swirl[4], heat[4];
+    double uwx[4], uwy[4], omega[4], Tw[4];
+    double scale;             // storage scale of the deviations (16-bit)
+};
+
+struct Launch {
+    int seg_rows;             // rows per z-segment
+    int warps_per_block;
+};
+
+// One time step src -> dst.
+cudaError_t launch_step(const HostParams &p, const Launch &l, const void *src, void *dst,
+                        cudaStream_t s);
+// Pre-collision fields of rows [row0, row1) into out[5][row1-row0][nr] (double).
+cudaError_t launch_fields(const HostParams &p, const Launch &l, const void *src, double *out,
+                          int row0, int row1, cudaStream_t s);
+// Diagnostics of the stored state src: block partial sums (partial), the
+// pre-collision T field (tfield, nz * nr doubles of scratch) and the final
+// values in result[NSUM]: 0 sum(rho - rho0), 1 sum((rho - rho0) y), 2 sum T,
+// 3 max |u|, 4..7 Nusselt number per side, 8 divergence flag.
+cudaError_t launch_diag(const HostParams &p, const Launch &l, const void *src, double *partial,
+                        double *tfield, double *result, cudaStream_t s);
+// Equilibria of host-format fields [5][rows][nr] (double) into rows [row0,row1) of dst.
+cudaError_t launch_init_fields(const HostParams &p, const double *fields, void *dst, int row0,
+                               int row1, cudaStream_t s);
+// Absolute distributions [19][rows][nr] (double) <-> storage, rows [row0,row1).
+cudaError_t launch_export(const HostParams &p, const void *src, double *out, int row0, int row1,
+                          cudaStream_t s);
+cudaError_t launch_import(const HostParams &p, const double *in, void *dst, int row0, int row1,
+                          cudaStream_t s);
+
+size_t storage_bytes(int storage);
+Launch default_launch(const HostParams &p);
+
+}  // namespace lbk

@@ -1,0 +1,892 @@
+// Fused time-step kernel of the axisymmetric thermal cascaded LB method
+// (arXiv 1806.10241) for sm_103a, plus the field, diagnostic and
+// import/export kernels.
+//
+// Data layout (per lattice, per buffer): 19 planes [q][z][pitch] of the
+// storage type: f0..f8, g0..g4, h0..h4 in the velocity order of Eq. 10 and
+// Eq. 28.  f and h are stored as deviations from the rest state (w_a rho0,
+// w_a T0), g as is, all multiplied by `scale` (1 except for FP16).
+//
+// Work decomposition: one thread owns one radial column c and marches along
+// z over a segment of rows.  Each plane row is loaded once, at the thread's
+// own column (aligned, coalesced 128-byte rows per warp).  Pull streaming
+// (Eq. 16b, 33b, 46b) shifts in r by warp shuffles and in z by carrying the
+// row groups in registers: populations with e_x = +1 come from the previous
+// row, e_x = 0 from the current row and e_x = -1 from the next row.  The
+// macroscopic fields of the stored (previous time level) state -- the
+// moments of the same loaded values -- give the central differences of the
+// geometric sources.  A warp covers 32 columns and updates the 30 inner
+// ones; lanes 0 and 31 are halo columns.  HBM traffic is therefore 19 loads
+// and 19 stores per node update.
+#include <algorithm>
+#include <type_traits>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "lb_internal.h"
+
+namespace lbk {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int OUT_COLS = 30;  // columns updated per warp
+
+// ---- storage conversions ------------------------------------------------
+
+template <typename S, typename C> struct Cvt;
+template <> struct Cvt<double, double> {
+    static __device__ __forceinline__ double ld(const double *p) { return *p; }
+    static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
+};
+template <> struct Cvt<float, float> {
+    static __device__ __forceinline__ float ld(const float *p) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <> struct Cvt<__nv_bfloat16, float> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <> struct Cvt<__half, float> {
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+};
+
+// ---- kernel parameters in the compute type --------------------------------
+
+template <typename C> struct KP {
+    int nr, nz, pitch, xper;
+    long long plane;
+    double r0;
+    C om3, om4, omhi, omg, omh;
+    C nu, alpha, gbeta, T0, bfx, rho0;
+    int planar, sign_lit, explicit_src;
+    int flow[4], swirl[4], heat[4];
+    C uwx[4], uwy[4], omega[4], Tw[4];
+    C scale, inv_scale;
+    // Nusselt scales per side (diagnostics)
+    double nu_scale[4];
+};
+
+template <typename C> KP<C> make_kp(const HostParams &h)
+{
+    KP<C> k;
+    k.nr = h.nr;
+    k.nz = h.nz;
+    k.pitch = h.pitch;
+    k.plane = h.plane;
+    k.xper = h.flow[0] == 2;
+    k.r0 = h.r0;
+    const double omn = 1.0 / (3.0 * h.nu + 0.5), oma = 1.0 / (3.0 * h.alpha + 0.5);
+    k.om3 = (C)h.omega3;
+    k.om4 = (C)omn;
+    k.omhi = (C)h.omega_hi;
+    k.omg = (C)omn;
+    k.omh = (C)oma;
+    k.nu = (C)h.nu;
+    k.alpha = (C)h.alpha;
+    k.gbeta = (C)h.g_beta;
+    k.T0 = (C)h.T0;
+    k.bfx = (C)h.body_fx;
+    k.rho0 = (C)h.rho0;
+    k.planar = h.planar;
+    k.sign_lit = h.sign_literal;
+    k.explicit_src = h.explicit_sources;
+    for (int s = 0; s < 4; ++s) {
+        k.flow[s] = h.flow[s];
+        k.swirl[s] = h.swirl[s];
+        k.heat[s] = h.heat[s];
+        k.uwx[s] = (C)h.uwx[s];
+        k.uwy[s] = (C)h.uwy[s];
+        k.omega[s] = (C)h.omega[s];
+        k.Tw[s] = (C)h.Tw[s];
+    }
+    k.scale = (C)h.scale;
+    k.inv_scale = (C)(1.0 / h.scale);
+    // Nusselt normalisation (Sec. 3.2): lateral walls -R_w / (H dT), end
+    // walls -(H / dT) * 2 / (R_o^2 - R_i^2); dT from the Dirichlet values.
+    double tmin = 0, tmax = 0;
+    int nd = 0;
+    for (int s = 0; s < 4; ++s)
+        if (h.heat[s] == 0) {
+            if (nd == 0 || h.Tw[s] < tmin) tmin = h.Tw[s];
+            if (nd == 0 || h.Tw[s] > tmax) tmax = h.Tw[s];
+            ++nd;
+        }
+    const double dT = (nd >= 2 && tmax > tmin) ? tmax - tmin : 1.0;
+    const double H = h.nz, Ri = h.r0, Ro = h.r0 + h.nr;
+    k.nu_scale[0] = k.nu_scale[1] = -(H / dT) * 2.0 / (Ro * Ro - Ri * Ri);
+    k.nu_scale[2] = -Ri / (H * dT);
+    k.nu_scale[3] = -Ro / (H * dT);
+    return k;
+}
+
+// ---- per-row helpers -------------------------------------------------------
+
+// Plane indices
+enum { F0 = 0, G0 = 9, H0 = 14 };
+
+template <typename C> struct PM {  // macroscopic fields of the stored state
+    C rd, ux, uy, ut, T;
+};
+
+template <typename C> __device__ __forceinline__ PM<C> moments(const C v[NQ], const KP<C> &k)
+{
+    // rho = rho0 + sum f_dev, j = sum f_dev e, psi = sum g, T = T0 + sum h_dev
+    const C is = k.inv_scale;
+    const C rd = (v[0] + v[1] + v[2] + v[3] + v[4] + v[5] + v[6] + v[7] + v[8]) * is;
+    const C jx = (v[1] - v[3] + v[5] - v[6] - v[7] + v[8]) * is;
+    const C jy = (v[2] - v[4] + v[5] + v[6] - v[7] - v[8]) * is;
+    const C ps = (v[9] + v[10] + v[11] + v[12] + v[13]) * is;
+    const C td = (v[14] + v[15] + v[16] + v[17] + v[18]) * is;
+    const C ir = (C)1 / (k.rho0 + rd);
+    PM<C> m;
+    m.rd = rd;
+    m.ux = jx * ir;
+    m.uy = jy * ir;
+    m.ut = ps * ir;
+    m.T = k.T0 + td;
+    return m;
+}
+
+template <typename C> __device__ __forceinline__ C shup(C v) { return __shfl_up_sync(FULL, v, 1); }
+template <typename C> __device__ __forceinline__ C shdn(C v) { return __shfl_down_sync(FULL, v, 1); }
+
+// Row groups (already shifted in r):
+//   XM (from row i-1): f1, f5, f8, g1, h1
+//   X0 (from row i)  : f0, f2, f4, g0, g2, g4, h0, h2, h4
+//   XP (from row i+1): f3, f6, f7, g3, h3
+template <typename C>
+__device__ __forceinline__ void groups(const C v[NQ], C xm[5], C x0[9], C xp[5])
+{
+    xm[0] = v[1];
+    xm[1] = shup(v[5]);
+    xm[2] = shdn(v[8]);
+    xm[3] = v[G0 + 1];
+    xm[4] = v[H0 + 1];
+    x0[0] = v[0];
+    x0[1] = shup(v[2]);
+    x0[2] = shdn(v[4]);
+    x0[3] = v[G0 + 0];
+    x0[4] = shup(v[G0 + 2]);
+    x0[5] = shdn(v[G0 + 4]);
+    x0[6] = v[H0 + 0];
+    x0[7] = shup(v[H0 + 2]);
+    x0[8] = shdn(v[H0 + 4]);
+    xp[0] = v[3];
+    xp[1] = shup(v[6]);
+    xp[2] = shdn(v[7]);
+    xp[3] = v[G0 + 3];
+    xp[4] = v[H0 + 3];
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ void load_row(const S *__restrict__ src, const KP<C> &k, int row, int col,
+                                         C v[NQ])
+{
+    const S *p = src + (long long)row * k.pitch + col;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = Cvt<S, C>::ld(p + q * k.plane);
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ C own(const S *__restrict__ src, const KP<C> &k, int q, int row, int col)
+{
+    return Cvt<S, C>::ld(src + q * k.plane + (long long)row * k.pitch + col);
+}
+
+// psi on a rotating wall: rho0 * omega * radius
+template <typename C> __device__ __forceinline__ C wall_psi(const KP<C> &k, int side, C y)
+{
+    const C radius = side <= 1 ? y : (side == 2 ? (C)k.r0 : (C)(k.r0 + k.nr));
+    return k.rho0 * k.omega[side] * radius;
+}
+
+// Scalar boundary value for the population entering from a wall (Sec. 3):
+// Dirichlet anti-bounce-back -x_own + 2 w s_w (w = 1/6, deviation form for h),
+// Neumann / even axis bounce-back x_own, odd axis (psi) -x_own.
+template <typename C>
+__device__ __forceinline__ C scalar_bc(int bc, C own_v, C wall_dev_scaled, bool odd_axis)
+{
+    if (bc == 0) return -own_v + (C)(2.0 / 6.0) * wall_dev_scaled;
+    if (bc == 2 && odd_axis) return -own_v;
+    return own_v;
+}
+
+// ---- the node update -------------------------------------------------------
+
+template <typename C> struct NodeOut {
+    C f[9], g[5], h[5];
+    C rho, ux, uy, ut, T;  // pre-collision fields
+};
+
+// Pulled (deviation, unscaled) values in fv/gv/hv; gradient inputs.
+template <typename C>
+__device__ __forceinline__ void update_node(const KP<C> &k, C y, C iy, C fv[9], C gv[5], C hv[5],
+                                            C dxuy, C dyux, C dyuy, C dyut, C dyT, NodeOut<C> &o)
+{
+    // output moments, Eq. 18, 35, 47 (deviation form: rest parts cancel)
+    const C rdo = fv[0] + fv[1] + fv[2] + fv[3] + fv[4] + fv[5] + fv[6] + fv[7] + fv[8];
+    const C jxo = fv[1] - fv[3] + fv[5] - fv[6] - fv[7] + fv[8];
+    const C jyo = fv[2] - fv[4] + fv[5] + fv[6] - fv[7] - fv[8];
+    const C pso = gv[0] + gv[1] + gv[2] + gv[3] + gv[4];
+    const C tdo = hv[0] + hv[1] + hv[2] + hv[3] + hv[4];
+
+    // sources (Eq. 4a-4c, 5, 7, 9) at the pre-collision state, two sweeps
+    C rd = rdo, jx = jxo, jy = jyo, ps = pso, td = tdo;
+    C MA = 0, Fx = 0, Fy = 0, Sps = 0, Sph = 0;
+    const int sweeps = k.explicit_src ? 1 : 2;
+    for (int sw = 0; sw < sweeps; ++sw) {
+        const C r = k.rho0 + rd, ir = (C)1 / r;
+        const C ux = jx * ir, uy = jy * ir, ph = k.T0 + td;
+        C MAs = 0, FAx = 0, FAy = 0;
+        Sps = 0;
+        Sph = 0;
+        if (!k.planar) {
+            const C mu = r * k.nu;
+            MAs = -jy * iy;
+            FAx = -jx * uy * iy + mu * (dxuy + dyux) * iy;
+            FAy = ps * ps * ir * iy - jy * uy * iy + (C)2 * mu * dyuy * iy - (C)2 * mu * uy * iy * iy;
+            Sps = (C)-2 * uy * ps * iy + mu * iy * dyut - k.nu * ps * iy * iy;
+            Sph = -uy * ph * iy + k.alpha * iy * dyT;
+        }
+        Fx = FAx + k.rho0 * k.gbeta * td + k.bfx;
+        Fy = FAy;
+        jx = jxo + (C)0.5 * Fx;
+        jy = jyo + (C)0.5 * Fy;
+        ps = pso + (C)0.5 * Sps;
+        td = tdo + (C)0.5 * Sph;
+        MA = (k.planar || k.explicit_src) ? MAs : -jy * iy;
+        rd = rdo + (C)0.5 * MA;
+    }
+    const C r = k.rho0 + rd, ir = (C)1 / r;
+    const C ux = jx * ir, uy = jy * ir;
+    const C phi = k.T0 + td;
+    o.rho = r;
+    o.ux = ux;
+    o.uy = uy;
+    o.ut = ps * ir;
+    o.T = phi;
+
+    // D2Q9 cascaded collision, Eq. 17 (raw moments of the streamed f; the
+    // rest-state parts rho0/3, rho0/9 written out)
+    const C third = (C)(1.0 / 3.0);
+    const C Dxx = fv[1] + fv[3] + fv[5] + fv[6] + fv[7] + fv[8];
+    const C Dyy = fv[2] + fv[4] + fv[5] + fv[6] + fv[7] + fv[8];
+    const C Dxy = fv[5] - fv[6] + fv[7] - fv[8];
+    const C Dxxy = fv[5] + fv[6] - fv[7] - fv[8];
+    const C Dxyy = fv[5] - fv[6] - fv[7] + fv[8];
+    const C Dxxyy = fv[5] + fv[6] + fv[7] + fv[8];
+    const C Kxx = k.rho0 * third + Dxx, Kyy = k.rho0 * third + Dyy;
+    const C ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const C p3 = k.om3 * (C)(1.0 / 12.0) * ((C)(2.0 / 3.0) * rd + r * (ux2 + uy2) - (Dxx + Dyy));
+    const C p4 = k.om4 * (C)0.25 * (r * (ux2 - uy2) - (Dxx - Dyy));
+    const C p5 = k.om4 * (C)0.25 * (r * uxy - Dxy);
+    const C q34p = (C)3 * p3 + p4, q34m = (C)3 * p3 - p4;
+    const C p6 = k.omhi * (C)0.25 * ((C)2 * r * ux2 * uy + Dxxy - (C)2 * ux * Dxy - uy * Kxx)
+                 - (C)0.5 * uy * q34p - (C)2 * ux * p5;
+    const C p7 = k.omhi * (C)0.25 * ((C)2 * r * ux * uy2 + Dxyy - (C)2 * uy * Dxy - ux * Kyy)
+                 - (C)0.5 * ux * q34m - (C)2 * uy * p5;
+    const C p8 = k.omhi * (C)0.25 *
+                     (rd * (C)(1.0 / 9.0) + (C)3 * r * ux2 * uy2 -
+                      (Dxxyy - (C)2 * ux * Dxyy - (C)2 * uy * Dxxy + ux2 * Kyy + uy2 * Kxx + (C)4 * uxy * Dxy)) -
+                 (C)2 * p3 - (C)0.5 * uy2 * q34p - (C)0.5 * ux2 * q34m - (C)4 * uxy * p5 - (C)2 * uy * p6 -
+                 (C)2 * ux * p7;
+    // source moments, Eq. 26
+    const C p0 = MA * (C)(1.0 / 9.0), p1 = Fx * (C)(1.0 / 6.0), p2 = Fy * (C)(1.0 / 6.0);
+    // back-transform, Eq. 27
+    o.f[0] = fv[0] + (p0 - (C)4 * (p3 - p8));
+    o.f[1] = fv[1] + (p0 + p1 - p3 + p4 + (C)2 * (p7 - p8));
+    o.f[2] = fv[2] + (p0 + p2 - p3 - p4 + (C)2 * (p6 - p8));
+    o.f[3] = fv[3] + (p0 - p1 - p3 + p4 - (C)2 * (p7 + p8));
+    o.f[4] = fv[4] + (p0 - p2 - p3 - p4 - (C)2 * (p6 + p8));
+    o.f[5] = fv[5] + (p0 + p1 + p2 + (C)2 * p3 + p5 - p6 - p7 + p8);
+    o.f[6] = fv[6] + (p0 - p1 + p2 + (C)2 * p3 - p5 - p6 + p7 + p8);
+    o.f[7] = fv[7] + (p0 - p1 - p2 + (C)2 * p3 + p5 + p6 + p7 + p8);
+    o.f[8] = fv[8] + (p0 + p1 - p2 + (C)2 * p3 - p5 + p6 - p7 + p8);
+
+    // D2Q5 cascaded collisions, Eq. 34 (psi) and Eq. 49 (T), with the sign
+    // that makes the equilibrium a fixed point unless sign_lit is set
+    const C sg = k.sign_lit ? (C)1 : (C)-1;
+    const C uu = ux2 + uy2, ud = ux2 - uy2;
+    {
+        const C kx = gv[1] - gv[3], ky = gv[2] - gv[4];
+        const C kxx = gv[1] + gv[3], kyy = gv[2] + gv[4];
+        const C q1 = k.omg * (C)0.5 * (ps * ux - kx);
+        const C q2 = k.omg * (C)0.5 * (ps * uy - ky);
+        const C q3 = k.omhi * (C)0.25 * ((C)(2.0 / 3.0) * ps - (kxx + kyy) + (C)2 * (ux * kx + uy * ky) + sg * uu * ps)
+                     + ux * q1 + uy * q2;
+        const C q4 = k.omhi * (C)0.25 * (-(kxx - kyy) + (C)2 * (ux * kx - uy * ky) + sg * ud * ps) + ux * q1 - uy * q2;
+        const C q0 = Sps * (C)0.2;  // Eq. 41
+        // Eq. 42
+        o.g[0] = gv[0] + (q0 - (C)4 * q3);
+        o.g[1] = gv[1] + (q0 + q1 + q3 + q4);
+        o.g[2] = gv[2] + (q0 + q2 + q3 - q4);
+        o.g[3] = gv[3] + (q0 - q1 + q3 + q4);
+        o.g[4] = gv[4] + (q0 - q2 + q3 - q4);
+    }
+    {
+        const C kx = hv[1] - hv[3], ky = hv[2] - hv[4];
+        const C Hxx = hv[1] + hv[3], Hyy = hv[2] + hv[4];
+        const C r1 = k.omh * (C)0.5 * (phi * ux - kx);
+        const C r2 = k.omh * (C)0.5 * (phi * uy - ky);
+        const C r3 = k.omhi * (C)0.25 * ((C)(2.0 / 3.0) * td - (Hxx + Hyy) + (C)2 * (ux * kx + uy * ky) + sg * uu * phi)
+                     + ux * r1 + uy * r2;
+        const C r4 = k.omhi * (C)0.25 * (-(Hxx - Hyy) + (C)2 * (ux * kx - uy * ky) + sg * ud * phi) + ux * r1 - uy * r2;
+        const C r0 = Sph * (C)0.2;  // Eq. 51
+        // Eq. 52
+        o.h[0] = hv[0] + (r0 - (C)4 * r3);
+        o.h[1] = hv[1] + (r0 + r1 + r3 + r4);
+        o.h[2] = hv[2] + (r0 + r2 + r3 - r4);
+        o.h[3] = hv[3] + (r0 - r1 + r3 + r4);
+        o.h[4] = hv[4] + (r0 - r2 + r3 - r4);
+    }
+}
+
+// ---- diagnostics accumulator ------------------------------------------------
+
+struct DiagAcc {
+    double mass_dev, mass_r_dev, tsum, umax, bad;
+};
+
+// ---- the march ---------------------------------------------------------------
+
+template <typename S, typename C, int MODE>
+__device__ __forceinline__ void march(const KP<C> &k, const S *__restrict__ src, S *__restrict__ dst,
+                                      double *__restrict__ fout, int fout_row0, int c, int row_s,
+                                      int row_e, DiagAcc *acc)
+{
+    const int lane = threadIdx.x & 31;
+    const int nr = k.nr, nz = k.nz;
+    const int cl = c < 0 ? 0 : (c >= nr ? nr - 1 : c);
+    const bool out_lane = lane >= 1 && lane <= OUT_COLS && c < nr;
+    const bool at_c0 = c == 0, at_cN = c == nr - 1;
+    const bool edge_warp = __any_sync(FULL, at_c0 || at_cN);
+    // radius of the column, its inverse computed in FP64 and rounded once
+    const double yd = k.r0 + cl + 0.5;
+    const C y = (C)yd, iy = (C)(1.0 / yd);
+    const C is = k.inv_scale, sc = k.scale;
+
+    C v[NQ];
+    C xm_prev[5], xm_cur[5], x0_cur[9];
+    PM<C> pm_cur;
+    C uy_prev = 0;
+    bool has_m;
+
+    // prologue: rows s-1 and s
+    if (row_s > 0 || k.xper) {
+        const int rm = row_s > 0 ? row_s - 1 : nz - 1;
+        load_row<S, C>(src, k, rm, cl, v);
+        C x0t[9], xpt[5];
+        groups<C>(v, xm_prev, x0t, xpt);
+        uy_prev = moments<C>(v, k).uy;
+        has_m = true;
+    } else {
+        has_m = false;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) xm_prev[q] = 0;
+    }
+    {
+        load_row<S, C>(src, k, row_s, cl, v);
+        C xpt[5];
+        groups<C>(v, xm_cur, x0_cur, xpt);
+        pm_cur = moments<C>(v, k);
+    }
+
+    for (int i = row_s; i < row_e; ++i) {
+        const bool has_p = (i + 1 < nz) || k.xper;
+        C xp_n[5], x0_n[9], xm_n[5];
+        PM<C> pm_n;
+        if (has_p) {
+            const int rp = i + 1 < nz ? i + 1 : 0;
+            load_row<S, C>(src, k, rp, cl, v);
+            groups<C>(v, xm_n, x0_n, xp_n);
+            pm_n = moments<C>(v, k);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) xp_n[q] = xm_n[q] = 0;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) x0_n[q] = 0;
+            pm_n = pm_cur;
+        }
+
+        // pulled values (scaled storage units)
+        C fv[9], gv[5], hv[5];
+        fv[1] = xm_prev[0]; fv[5] = xm_prev[1]; fv[8] = xm_prev[2]; gv[1] = xm_prev[3]; hv[1] = xm_prev[4];
+        fv[0] = x0_cur[0]; fv[2] = x0_cur[1]; fv[4] = x0_cur[2];
+        gv[0] = x0_cur[3]; gv[2] = x0_cur[4]; gv[4] = x0_cur[5];
+        hv[0] = x0_cur[6]; hv[2] = x0_cur[7]; hv[4] = x0_cur[8];
+        fv[3] = xp_n[0]; fv[6] = xp_n[1]; fv[7] = xp_n[2]; gv[3] = xp_n[3]; hv[3] = xp_n[4];
+
+        // lateral boundaries (Sec. 3): the population entering from r < r0 or
+        // r > r0 + nr is rebuilt from the node's own stored values
+        if (edge_warp) {
+            if (at_c0) {
+                const int sd = 2;
+                const C rw = k.rho0 * sc;
+                if (k.flow[sd] == 1) {  // axis: mirror images
+                    fv[2] = own<S, C>(src, k, 4, i, 0);
+                    if (has_m) fv[5] = own<S, C>(src, k, 8, i > 0 ? i - 1 : nz - 1, 0);
+                    if (has_p) fv[6] = own<S, C>(src, k, 7, i + 1 < nz ? i + 1 : 0, 0);
+                } else {  // wall: bounce-back + moving-wall term 6 w rho0 (e.u_w)
+                    const C ux_w = k.uwx[sd], uy_w = k.uwy[sd];
+                    fv[2] = own<S, C>(src, k, 4, i, 0) + rw * (C)(6.0 / 9.0) * uy_w;
+                    fv[5] = own<S, C>(src, k, 7, i, 0) + rw * (C)(6.0 / 36.0) * (ux_w + uy_w);
+                    fv[6] = own<S, C>(src, k, 8, i, 0) + rw * (C)(6.0 / 36.0) * (-ux_w + uy_w);
+                }
+                gv[2] = scalar_bc<C>(k.swirl[sd], own<S, C>(src, k, G0 + 4, i, 0), wall_psi<C>(k, sd, y) * sc, true);
+                hv[2] = scalar_bc<C>(k.heat[sd], own<S, C>(src, k, H0 + 4, i, 0), (k.Tw[sd] - k.T0) * sc, false);
+            }
+            if (at_cN) {
+                const int sd = 3;
+                const C rw = k.rho0 * sc;
+                const C ux_w = k.uwx[sd], uy_w = k.uwy[sd];
+                fv[4] = own<S, C>(src, k, 2, i, nr - 1) + rw * (C)(6.0 / 9.0) * (-uy_w);
+                fv[7] = own<S, C>(src, k, 5, i, nr - 1) + rw * (C)(6.0 / 36.0) * (-ux_w - uy_w);
+                fv[8] = own<S, C>(src, k, 6, i, nr - 1) + rw * (C)(6.0 / 36.0) * (ux_w - uy_w);
+                gv[4] = scalar_bc<C>(k.swirl[sd], own<S, C>(src, k, G0 + 2, i, nr - 1), wall_psi<C>(k, sd, y) * sc, true);
+                hv[4] = scalar_bc<C>(k.heat[sd], own<S, C>(src, k, H0 + 2, i, nr - 1), (k.Tw[sd] - k.T0) * sc, false);
+            }
+        }
+        // end walls (rows 0 and nz-1 unless periodic); they win in corners
+        if (!has_m) {
+            const int sd = 0;
+            const C rw = k.rho0 * sc, ux_w = k.uwx[sd], uy_w = k.uwy[sd];
+            fv[1] = own<S, C>(src, k, 3, i, cl) + rw * (C)(6.0 / 9.0) * ux_w;
+            fv[5] = own<S, C>(src, k, 7, i, cl) + rw * (C)(6.0 / 36.0) * (ux_w + uy_w);
+            fv[8] = own<S, C>(src, k, 6, i, cl) + rw * (C)(6.0 / 36.0) * (ux_w - uy_w);
+            gv[1] = scalar_bc<C>(k.swirl[sd], own<S, C>(src, k, G0 + 3, i, cl), wall_psi<C>(k, sd, y) * sc, true);
+            hv[1] = scalar_bc<C>(k.heat[sd], own<S, C>(src, k, H0 + 3, i, cl), (k.Tw[sd] - k.T0) * sc, false);
+        }
+        if (!has_p) {
+            const int sd = 1;
+            const C rw = k.rho0 * sc, ux_w = k.uwx[sd], uy_w = k.uwy[sd];
+            fv[3] = own<S, C>(src, k, 1, i, cl) + rw * (C)(6.0 / 9.0) * (-ux_w);
+            fv[6] = own<S, C>(src, k, 8, i, cl) + rw * (C)(6.0 / 36.0) * (-ux_w + uy_w);
+            fv[7] = own<S, C>(src, k, 5, i, cl) + rw * (C)(6.0 / 36.0) * (-ux_w - uy_w);
+            gv[3] = scalar_bc<C>(k.swirl[sd], own<S, C>(src, k, G0 + 1, i, cl), wall_psi<C>(k, sd, y) * sc, true);
+            hv[3] = scalar_bc<C>(k.heat[sd], own<S, C>(src, k, H0 + 1, i, cl), (k.Tw[sd] - k.T0) * sc, false);
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) fv[q] *= is;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            gv[q] *= is;
+            hv[q] *= is;
+        }
+
+        // central differences of the stored-state fields, with ghosts
+        const C uy_xm = has_m ? uy_prev : (C)2 * k.uwy[0] - pm_cur.uy;
+        const C uy_xp = has_p ? pm_n.uy : (C)2 * k.uwy[1] - pm_cur.uy;
+        C ux_l = shup(pm_cur.ux), uy_l = shup(pm_cur.uy), ut_l = shup(pm_cur.ut), T_l = shup(pm_cur.T);
+        C ux_r = shdn(pm_cur.ux), uy_r = shdn(pm_cur.uy), ut_r = shdn(pm_cur.ut), T_r = shdn(pm_cur.T);
+        if (edge_warp) {
+            if (at_c0) {
+                const int sd = 2;
+                if (k.flow[sd] == 1) {
+                    ux_l = pm_cur.ux;
+                    uy_l = -pm_cur.uy;
+                } else {
+                    ux_l = (C)2 * k.uwx[sd] - pm_cur.ux;
+                    uy_l = (C)2 * k.uwy[sd] - pm_cur.uy;
+                }
+                const int sw = k.swirl[sd], ht = k.heat[sd];
+                ut_l = sw == 2 ? -pm_cur.ut : (sw == 0 ? (C)2 * k.omega[sd] * (C)k.r0 - pm_cur.ut : pm_cur.ut);
+                T_l = ht == 0 ? (C)2 * k.Tw[sd] - pm_cur.T : pm_cur.T;
+            }
+            if (at_cN) {
+                const int sd = 3;
+                ux_r = (C)2 * k.uwx[sd] - pm_cur.ux;
+                uy_r = (C)2 * k.uwy[sd] - pm_cur.uy;
+                const int sw = k.swirl[sd], ht = k.heat[sd];
+                ut_r = sw == 0 ? (C)2 * k.omega[sd] * (C)(k.r0 + k.nr) - pm_cur.ut : pm_cur.ut;
+                T_r = ht == 0 ? (C)2 * k.Tw[sd] - pm_cur.T : pm_cur.T;
+            }
+        }
+        const C dxuy = (C)0.5 * (uy_xp - uy_xm);
+        const C dyux = (C)0.5 * (ux_r - ux_l);
+        const C dyuy = (C)0.5 * (uy_r - uy_l);
+        const C dyut = (C)0.5 * (ut_r - ut_l);
+        const C dyT = (C)0.5 * (T_r - T_l);
+
+        NodeOut<C> o;
+        update_node<C>(k, y, iy, fv, gv, hv, dxuy, dyux, dyuy, dyut, dyT, o);
+
+        if (MODE == MODE_STEP) {
+            if (out_lane) {
+                S *p = dst + (long long)i * k.pitch + c;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) Cvt<S, C>::st(p + q * k.plane, o.f[q] * sc);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) Cvt<S, C>::st(p + (G0 + q) * k.plane, o.g[q] * sc);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) Cvt<S, C>::st(p + (H0 + q) * k.plane, o.h[q] * sc);
+            }
+        } else if (MODE == MODE_FIELDS) {
+            if (out_lane) {
+                const long long n = (long long)(row_e - fout_row0) * nr;
+                double *p = fout + (long long)(i - fout_row0) * nr + c;
+                p[0] = (double)o.rho;
+                p[n] = (double)o.ux;
+                p[2 * n] = (double)o.uy;
+                p[3 * n] = (double)o.ut;
+                p[4 * n] = (double)o.T;
+            }
+        } else {  // MODE_DIAG
+            if (out_lane) {
+                const double rdp = (double)pm_cur.rd;
+                acc->mass_dev += rdp;
+                acc->mass_r_dev += rdp * yd;
+                acc->tsum += (double)o.T;
+                const double um = sqrt((double)o.ux * (double)o.ux + (double)o.uy * (double)o.uy);
+                acc->umax = fmax(acc->umax, um);
+                const bool finite = isfinite((double)o.rho) && isfinite((double)o.ux) &&
+                                    isfinite((double)o.uy) && isfinite((double)o.ut) &&
+                                    isfinite((double)o.T);
+                if (!finite || o.rho < (C)0.5 || o.rho > (C)1.5) acc->bad = 1.0;
+                fout[(long long)i * nr + c] = (double)o.T;  // for the wall fluxes
+            }
+        }
+
+        // rotate the row window
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            xm_prev[q] = xm_cur[q];
+            xm_cur[q] = xm_n[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) x0_cur[q] = x0_n[q];
+        uy_prev = pm_cur.uy;
+        pm_cur = pm_n;
+        has_m = true;
+    }
+}
+
+template <typename S, typename C>
+__global__ void __launch_bounds__(256) k_step(KP<C> k, const S *__restrict__ src, S *__restrict__ dst,
+                                              int seg_rows, int nwin)
+{
+    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (warp >= nwin) return;  // whole warps only
+    const int c = warp * OUT_COLS - 1 + (threadIdx.x & 31);
+    const int s = blockIdx.y * seg_rows;
+    const int e = min(k.nz, s + seg_rows);
+    march<S, C, MODE_STEP>(k, src, dst, nullptr, 0, c, s, e, nullptr);
+}
+
+template <typename S, typename C>
+__global__ void __launch_bounds__(256) k_fields(KP<C> k, const S *__restrict__ src, double *__restrict__ out,
+                                                int row0, int row1, int nwin)
+{
+    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (warp >= nwin) return;
+    const int c = warp * OUT_COLS - 1 + (threadIdx.x & 31);
+    march<S, C, MODE_FIELDS>(k, src, nullptr, out, row0, c, row0, row1, nullptr);
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(FULL, v, o));
+    return v;
+}
+
+// One warp per 30-column window, whole height (the end-wall fluxes need rows
+// 0, 1 and nz-2, nz-1 in the same march).  Block partial sums in a fixed
+// order, then a single-block final reduction: deterministic.
+template <typename S, typename C>
+__global__ void __launch_bounds__(128) k_diag(KP<C> k, const S *__restrict__ src, double *__restrict__ partial,
+                                              double *__restrict__ tfield, int seg_rows, int nwin)
+{
+    __shared__ double sh[4][NSUM];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+    DiagAcc a = {0, 0, 0, 0, 0};
+    if (warp < nwin) {
+        const int c = warp * OUT_COLS - 1 + lane;
+        const int s = blockIdx.y * seg_rows, e = min(k.nz, s + seg_rows);
+        march<S, C, MODE_DIAG>(k, src, nullptr, tfield, 0, c, s, e, &a);
+    }
+    double vals[NSUM] = {a.mass_dev, a.mass_r_dev, a.tsum, a.umax, 0, 0, 0, 0, a.bad, 0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < NSUM; ++q) vals[q] = (q == 3 || q == 8) ? warp_max(vals[q]) : warp_sum(vals[q]);
+    if (lane == 0)
+        for (int q = 0; q < NSUM; ++q) sh[wib][q] = vals[q];
+    __syncthreads();
+    if (threadIdx.x < NSUM) {
+        const int q = threadIdx.x;
+        double r = sh[0][q];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = (q == 3 || q == 8) ? fmax(r, sh[w][q]) : r + sh[w][q];
+        partial[(blockIdx.y * gridDim.x + blockIdx.x) * NSUM + q] = r;
+    }
+}
+
+// Wall heat-flux sums (Sec. 3.2) from the pre-collision T field: one-sided
+// second-order derivative through the wall value, wall half a cell away,
+// (-8 T_w + 9 T_1 - T_2) / 3 along the inward direction; end walls weighted
+// by the radius.  One block, fixed-order tree reduction (deterministic).
+template <typename C>
+__global__ void __launch_bounds__(256) k_wall(KP<C> k, const double *__restrict__ T, double *__restrict__ result)
+{
+    __shared__ double sh[256];
+    const int nr = k.nr, nz = k.nz;
+    for (int sd = 0; sd < 4; ++sd) {
+        double acc = 0;
+        if (k.heat[sd] == 0) {
+            const double Tw = (double)k.Tw[sd];
+            if (sd == 2)
+                for (int i = threadIdx.x; i < nz; i += blockDim.x)
+                    acc += (-8.0 * Tw + 9.0 * T[(long long)i * nr] - T[(long long)i * nr + 1]) / 3.0;
+            else if (sd == 3)
+                for (int i = threadIdx.x; i < nz; i += blockDim.x)
+                    acc += (8.0 * Tw - 9.0 * T[(long long)i * nr + nr - 1] + T[(long long)i * nr + nr - 2]) / 3.0;
+            else if (sd == 0)
+                for (int j = threadIdx.x; j < nr; j += blockDim.x)
+                    acc += (k.r0 + j + 0.5) * (-8.0 * Tw + 9.0 * T[j] - T[nr + j]) / 3.0;
+            else
+                for (int j = threadIdx.x; j < nr; j += blockDim.x)
+                    acc += (k.r0 + j + 0.5) *
+                           (8.0 * Tw - 9.0 * T[(long long)(nz - 1) * nr + j] + T[(long long)(nz - 2) * nr + j]) / 3.0;
+        }
+        sh[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) result[4 + sd] = k.heat[sd] == 0 ? sh[0] * k.nu_scale[sd] : 0.0;
+        __syncthreads();
+    }
+}
+
+__global__ void k_diag_final(const double *__restrict__ partial, int nblocks, double *__restrict__ result)
+{
+    const int q = threadIdx.x;
+    if (q >= NSUM || (q >= 4 && q < 8)) return;  // 4..7: wall sums (k_wall)
+    double r = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double v = partial[b * NSUM + q];
+        r = (q == 3 || q == 8) ? fmax(r, v) : r + v;
+    }
+    result[q] = r;
+}
+
+// ---- initialisation and exchange ---------------------------------------------
+
+// D2Q9 equilibrium with Maxwellian raw moments, factorised per axis
+__device__ __forceinline__ double axis_factor(int e, double u)
+{
+    const double c2 = 1.0 / 3.0;
+    return e == 0 ? 1.0 - c2 - u * u : 0.5 * (c2 + u * u + e * u);
+}
+
+__constant__ int c_ex9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int c_ey9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+__constant__ double c_w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+__constant__ double c_w5[5] = {1.0 / 3, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6};
+
+__device__ __forceinline__ void eq_d2q5(double s, double ux, double uy, double o[5])
+{
+    const double c2 = 1.0 / 3.0;
+    o[0] = s * (1.0 - 2.0 * c2 - ux * ux - uy * uy);
+    o[1] = 0.5 * s * (c2 + ux * ux + ux);
+    o[3] = 0.5 * s * (c2 + ux * ux - ux);
+    o[2] = 0.5 * s * (c2 + uy * uy + uy);
+    o[4] = 0.5 * s * (c2 + uy * uy - uy);
+}
+
+template <typename S>
+__global__ void k_init_fields(HostParams h, const double *__restrict__ fields, S *__restrict__ dst, int row0,
+                              int row1)
+{
+    const long long nrow = row1 - row0;
+    const long long n = nrow * h.nr;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int i = row0 + (int)(t / h.nr), j = (int)(t % h.nr);
+        const double rho = fields[t], ux = fields[n + t], uy = fields[2 * n + t];
+        const double ut = fields[3 * n + t], T = fields[4 * n + t];
+        S *p = dst + (long long)i * h.pitch + j;
+        for (int a = 0; a < 9; ++a) {
+            const double fe = rho * axis_factor(c_ex9[a], ux) * axis_factor(c_ey9[a], uy);
+            Cvt<S, typename std::conditional<std::is_same<S, double>::value, double, float>::type>::st(
+                p + a * h.plane, (fe - c_w9[a] * h.rho0) * h.scale);
+        }
+        double ge[5], he[5];
+        eq_d2q5(rho * ut, ux, uy, ge);
+        eq_d2q5(T, ux, uy, he);
+        for (int a = 0; a < 5; ++a) {
+            Cvt<S, typename std::conditional<std::is_same<S, double>::value, double, float>::type>::st(
+                p + (G0 + a) * h.plane, ge[a] * h.scale);
+            Cvt<S, typename std::conditional<std::is_same<S, double>::value, double, float>::type>::st(
+                p + (H0 + a) * h.plane, (he[a] - c_w5[a] * h.T0) * h.scale);
+        }
+    }
+}
+
+template <typename S>
+__global__ void k_export(HostParams h, const S *__restrict__ src, double *__restrict__ out, int row0, int row1)
+{
+    using C = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
+    const long long n = (long long)(row1 - row0) * h.nr;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int i = row0 + (int)(t / h.nr), j = (int)(t % h.nr);
+        const S *p = src + (long long)i * h.pitch + j;
+        for (int q = 0; q < NQ; ++q) {
+            double rest = q < 9 ? c_w9[q] * h.rho0 : (q < 14 ? 0.0 : c_w5[q - 14] * h.T0);
+            out[q * n + t] = (double)Cvt<S, C>::ld(p + q * h.plane) / h.scale + rest;
+        }
+    }
+}
+
+template <typename S>
+__global__ void k_import(HostParams h, const double *__restrict__ in, S *__restrict__ dst, int row0, int row1)
+{
+    using C = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
+    const long long n = (long long)(row1 - row0) * h.nr;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int i = row0 + (int)(t / h.nr), j = (int)(t % h.nr);
+        S *p = dst + (long long)i * h.pitch + j;
+        for (int q = 0; q < NQ; ++q) {
+            double rest = q < 9 ? c_w9[q] * h.rho0 : (q < 14 ? 0.0 : c_w5[q - 14] * h.T0);
+            Cvt<S, C>::st(p + q * h.plane, (C)((in[q * n + t] - rest) * h.scale));
+        }
+    }
+}
+
+int nwindows(int nr) { return (nr + OUT_COLS - 1) / OUT_COLS; }
+
+template <typename S, typename C>
+cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *dst, cudaStream_t s)
+{
+    const KP<C> k = make_kp<C>(h);
+    const int nwin = nwindows(h.nr);
+    const int wpb = l.warps_per_block;
+    const int seg = l.seg_rows;
+    dim3 grid((nwin + wpb - 1) / wpb, (h.nz + seg - 1) / seg);
+    k_step<S, C><<<grid, 32 * wpb, 0, s>>>(k, (const S *)src, (S *)dst, seg, nwin);
+    return cudaGetLastError();
+}
+
+template <typename S, typename C>
+cudaError_t fields_t(const HostParams &h, const Launch &l, const void *src, double *out, int row0, int row1,
+                     cudaStream_t s)
+{
+    const KP<C> k = make_kp<C>(h);
+    const int nwin = nwindows(h.nr);
+    const int wpb = l.warps_per_block;
+    dim3 grid((nwin + wpb - 1) / wpb, 1);
+    k_fields<S, C><<<grid, 32 * wpb, 0, s>>>(k, (const S *)src, out, row0, row1, nwin);
+    return cudaGetLastError();
+}
+
+template <typename S, typename C>
+cudaError_t diag_t(const HostParams &h, const Launch &l, const void *src, double *partial, double *tfield,
+                   double *result, cudaStream_t s)
+{
+    const KP<C> k = make_kp<C>(h);
+    const int nwin = nwindows(h.nr);
+    const int wpb = 4;
+    const int seg = l.seg_rows;
+    dim3 grid((nwin + wpb - 1) / wpb, (h.nz + seg - 1) / seg);
+    const int nb = grid.x * grid.y;
+    if (nb > MAX_DIAG_BLOCKS) return cudaErrorInvalidValue;
+    k_diag<S, C><<<grid, 32 * wpb, 0, s>>>(k, (const S *)src, partial, tfield, seg, nwin);
+    k_diag_final<<<1, 32, 0, s>>>(partial, nb, result);
+    k_wall<C><<<1, 256, 0, s>>>(k, tfield, result);
+    return cudaGetLastError();
+}
+
+int blocks_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 4096); }
+
+}  // namespace
+
+size_t storage_bytes(int storage)
+{
+    switch (storage) {
+        case ST_FP64: return 8;
+        case ST_FP32: return 4;
+        default: return 2;
+    }
+}
+
+Launch default_launch(const HostParams &p)
+{
+    Launch l;
+    l.warps_per_block = 4;
+    // aim for about 8 resident warps per SM-slot across 152 SMs
+    const int nwin = nwindows(p.nr);
+    const long long target_warps = 152LL * 24;
+    long long segs = (target_warps + nwin - 1) / nwin;
+    if (segs < 1) segs = 1;
+    int seg = (int)((p.nz + segs - 1) / segs);
+    if (seg < 8) seg = 8;
+    l.seg_rows = seg;
+    return l;
+}
+
+#define DISPATCH(p, CALL)                                                   \
+    switch ((p).storage) {                                                  \
+        case ST_FP64: { using S = double; using C = double; return CALL; }   \
+        case ST_FP32: { using S = float; using C = float; return CALL; }     \
+        case ST_BF16: { using S = __nv_bfloat16; using C = float; return CALL; } \
+        case ST_FP16: { using S = __half; using C = float; return CALL; }    \
+        default: return cudaErrorInvalidValue;                              \
+    }
+
+cudaError_t launch_step(const HostParams &p, const Launch &l, const void *src, void *dst, cudaStream_t s)
+{
+    DISPATCH(p, (step_t<S, C>(p, l, src, dst, s)));
+}
+
+cudaError_t launch_fields(const HostParams &p, const Launch &l, const void *src, double *out, int row0, int row1,
+                          cudaStream_t s)
+{
+    DISPATCH(p, (fields_t<S, C>(p, l, src, out, row0, row1, s)));
+}
+
+cudaError_t launch_diag(const HostParams &p, const Launch &l, const void *src, double *partial, double *tfield,
+                        double *result, cudaStream_t s)
+{
+    DISPATCH(p, (diag_t<S, C>(p, l, src, partial, tfield, result, s)));
+}
+
+#define DISPATCH_S(p, CALL)                                         \
+    switch ((p).storage) {                                          \
+        case ST_FP64: { using S = double; CALL; break; }            \
+        case ST_FP32: { using S = float; CALL; break; }             \
+        case ST_BF16: { using S = __nv_bfloat16; CALL; break; }     \
+        case ST_FP16: { using S = __half; CALL; break; }            \
+        default: return cudaErrorInvalidValue;                      \
+    }
+
+cudaError_t launch_init_fields(const HostParams &p, const double *fields, void *dst, int row0, int row1,
+                               cudaStream_t s)
+{
+    const int nb = blocks_for((long long)(row1 - row0) * p.nr);
+    DISPATCH_S(p, (k_init_fields<S><<<nb, 256, 0, s>>>(p, fields, (S *)dst, row0, row1)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(const HostParams &p, const void *src, double *out, int row0, int row1, cudaStream_t s)
+{
+    const int nb = blocks_for((long long)(row1 - row0) * p.nr);
+    DISPATCH_S(p, (k_export<S><<<nb, 256, 0, s>>>(p, (const S *)src, out, row0, row1)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import(const HostParams &p, const double *in, void *dst, int row0, int row1, cudaStream_t s)
+{
+    const int nb = blocks_for((long long)(row1 - row0) * p.nr);
+    DISPATCH_S(p, (k_import<S><<<nb, 256, 0, s>>>(p, in, (S *)dst, row0, row1)));
+    return cudaGetLastError();
+}
+
+}  // namespace lbk

@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Both sides start from the same seeded state.  FP64 storage must agree with
+the oracle to round-off (1e-12 absolute on distributions of size ~0.1-0.5).
+FP32 storage: distributions within 2e-6 absolute after a few steps (FP32
+unit round-off 6e-8 times the O(10) operations that touch each value, on
+values <= 0.5, with margin), and the velocity / swirl / temperature fields
+within 1e-5 relative L2 after 1000 steps, the mean Nusselt number within
+1e-4 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_10241_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_10241_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def Solver(*a, **k):
+    from paper_1806_10241_gb300.solver import Solver as S
+    return S(*a, **k)
+
+
+# ---- lattices covering every boundary rule ---------------------------------------
+
+def annulus_walls(nr, nz):
+    """Annulus, all four sides walls: sliding / porous walls, rotating walls,
+    Dirichlet and Neumann temperatures, buoyancy."""
+    sides = [W._side(heat=W.SC_DIRICHLET, T_w=0.9, omega=0.002, u_wx=0.0, u_wy=0.01),
+             W._side(heat=W.SC_NEUMANN, omega=-0.001, u_wy=-0.02),
+             W._side(heat=W.SC_DIRICHLET, T_w=1.0, omega=0.003, u_wx=0.015, u_wy=0.002),
+             W._side(heat=W.SC_NEUMANN, swirl=W.SC_NEUMANN, u_wx=-0.01)]
+    return {"nr": nr, "nz": nz, "r0": 5.0, "nu": 0.05, "alpha": 0.07, "g_beta": 1e-3, "T0": 0.5,
+            "rho0": 1.0, "omega3": 1.1, "omega_hi": 1.0, "sides": sides}
+
+
+def cylinder_axis(nr, nz):
+    sides = [W._side(heat=W.SC_DIRICHLET, T_w=1.0),
+             W._side(heat=W.SC_DIRICHLET, T_w=0.0, omega=0.004),
+             W._axis(),
+             W._side(heat=W.SC_NEUMANN, omega=0.001)]
+    return {"nr": nr, "nz": nz, "r0": 0.0, "nu": 0.04, "alpha": 0.06, "g_beta": 2e-3, "T0": 0.5,
+            "rho0": 1.0, "omega3": 1.0, "omega_hi": 1.0, "sides": sides}
+
+
+def periodic_annulus(nr, nz):
+    sides = [W._periodic(), W._periodic(),
+             W._side(heat=W.SC_DIRICHLET, T_w=1.0, omega=0.004, u_wy=0.01),
+             W._side(heat=W.SC_DIRICHLET, T_w=0.0, omega=-0.001, u_wy=0.005)]
+    return {"nr": nr, "nz": nz, "r0": 3.0, "nu": 0.08, "alpha": 0.05, "g_beta": 0.0, "T0": 0.5,
+            "rho0": 1.0, "body_fx": 1e-5, "omega3": 0.9, "omega_hi": 1.2, "sides": sides}
+
+
+def periodic_cylinder(nr, nz):
+    sides = [W._periodic(), W._periodic(), W._axis(), W._side(heat=W.SC_DIRICHLET, T_w=0.2, omega=0.01)]
+    return {"nr": nr, "nz": nz, "r0": 0.0, "nu": 0.1, "alpha": 0.1, "g_beta": 0.0, "T0": 0.5,
+            "rho0": 1.0, "body_fx": 2e-5, "sides": sides}
+
+
+def planar_box(nr, nz):
+    p = annulus_walls(nr, nz)
+    p["planar"] = 1
+    p["r0"] = 0.0
+    return p
+
+
+BUILDERS = {"annulus_walls": annulus_walls, "cylinder_axis": cylinder_axis,
+            "periodic_annulus": periodic_annulus, "periodic_cylinder": periodic_cylinder,
+            "planar_box": planar_box}
+SIZES = [(2, 2), (7, 9), (31, 5), (33, 17), (61, 13), (97, 33)]
+
+
+def random_state(params, seed):
+    """Seeded state: equilibria of random fields (oracle), then each
+    distribution value perturbed by up to 3 % (numpy)."""
+    rng = np.random.default_rng(seed)
+    nz, nr = params["nz"], params["nr"]
+    fields = np.empty((5, nz, nr))
+    fields[0] = 1.0 + 0.01 * rng.uniform(-1, 1, (nz, nr))
+    fields[1] = 0.04 * rng.uniform(-1, 1, (nz, nr))
+    fields[2] = 0.04 * rng.uniform(-1, 1, (nz, nr))
+    fields[3] = 0.03 * rng.uniform(-1, 1, (nz, nr))
+    fields[4] = rng.uniform(0, 1, (nz, nr))
+    o = oracle.Oracle(params)
+    o.init_fields(fields)
+    d = o.get_dist()
+    return d * (1.0 + 0.03 * rng.uniform(-1, 1, d.shape))
+
+
+def run_both(params, state, steps, storage, launch=(0, 0)):
+    g = Solver(params, storage=storage)
+    g.set_launch(*launch)
+    g.set_dist(state)
+    g.step(steps)
+    got = g.get_dist()
+    o = oracle.Oracle(params)
+    o.set_dist(state)
+    o.step(steps)
+    return got, o.get_dist(), g, o
+
+
+@pytest.mark.parametrize("name", list(BUILDERS))
+@pytest.mark.parametrize("nr,nz", SIZES)
+def test_fp64_distributions_match_oracle(name, nr, nz):
+    params = BUILDERS[name](nr, nz)
+    st = random_state(params, seed=nr * 1000 + nz)
+    for steps, launch in ((1, (0, 0)), (5, (3, 1))):
+        got, want, _, _ = run_both(params, st, steps, "fp64", launch)
+        err = np.max(np.abs(got - want))
+        assert err < 1e-12, (name, nr, nz, steps, err)
+
+
+@pytest.mark.parametrize("name", list(BUILDERS))
+@pytest.mark.parametrize("nr,nz", SIZES)
+def test_fp32_distributions_match_oracle(name, nr, nz):
+    params = BUILDERS[name](nr, nz)
+    st = random_state(params, seed=7 + nr * 1000 + nz)
+    for steps, launch in ((1, (0, 0)), (5, (4, 2))):
+        got, want, _, _ = run_both(params, st, steps, "fp32", launch)
+        err = np.max(np.abs(got - want))
+        assert err < 2e-6, (name, nr, nz, steps, err)
+
+
+def _rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("case", ["annulus_41", "cylinder_lid"])
+def test_fp32_fields_after_1000_steps(case):
+    if case == "annulus_41":
+        c = W.config_annulus_41()
+    else:
+        c = W.swirling_cylinder(nr=64, nz=128, Re=200.0, Ra=1e5, Pr=0.7, u_lid=0.05, amp=1e-6, seed=0)
+    g = Solver(c.params, storage="fp32")
+    g.init_fields(c.fields)
+    g.step(1000)
+    o = oracle.Oracle(c.params)
+    o.init_fields(c.fields)
+    o.step(1000)
+    got, want = g.fields(), o.fields()
+    for q in (1, 2, 3, 4):
+        if np.linalg.norm(want[q]) == 0:
+            assert np.max(np.abs(got[q])) < 1e-12
+            continue
+        assert _rel_l2(got[q], want[q]) < 1e-5, (case, q, _rel_l2(got[q], want[q]))
+    dg, do = g.diag(), o.diag()
+    assert dg["status"] == 0
+    assert dg["nu_avg"] == pytest.approx(do["nu_avg"], rel=1e-4)
+    assert dg["mass"] == pytest.approx(do["mass"], rel=1e-9)
+    assert dg["T_sum"] == pytest.approx(do["T_sum"], rel=1e-6)
+
+
+@pytest.mark.parametrize("name", ["annulus_walls", "cylinder_axis", "periodic_annulus"])
+def test_fp64_fields_and_diagnostics_match_oracle(name):
+    params = BUILDERS[name](45, 38)
+    st = random_state(params, seed=11)
+    got, want, g, o = run_both(params, st, 3, "fp64")
+    assert np.max(np.abs(g.fields() - o.fields())) < 1e-12
+    dg, do = g.diag(), o.diag()
+    for k in ("nu_i", "nu_o", "nu_avg", "mass", "mass_r", "T_sum", "u_max"):
+        assert dg[k] == pytest.approx(do[k], rel=1e-11, abs=1e-13), k
+    for s in range(4):
+        assert dg["nu_side"][s] == pytest.approx(do["nu_side"][s], rel=1e-11, abs=1e-13)
+
+
+def test_launch_shape_does_not_change_results():
+    params = cylinder_axis(97, 70)
+    st = random_state(params, seed=5)
+    ref = None
+    for launch in ((0, 0), (1, 1), (7, 2), (70, 4), (16, 8)):
+        got, _, _, _ = run_both(params, st, 4, "fp32", launch)
+        if ref is None:
+            ref = got
+        else:
+            assert np.array_equal(got, ref), launch
+
+
+def test_checkpoint_restore_is_bitwise():
+    c = W.swirling_cylinder(nr=50, nz=70, Re=300.0, Ra=1e4, amp=1e-3, seed=3)
+    a = Solver(c.params, storage="fp32")
+    a.init_fields(c.fields)
+    a.step(40)
+    full = a.get_dist()
+    b = Solver(c.params, storage="fp32")
+    b.init_fields(c.fields)
+    b.step(20)
+    blob = b.get_state()
+    b2 = Solver(c.params, storage="fp32")
+    b2.set_state(blob)
+    assert b2.step_count == 20
+    b2.step(20)
+    assert np.array_equal(b2.get_dist(), full)
+
+
+def test_full_size_cylinder_matches_oracle():
+    """The benchmark lattice (1024 x 2048, FP32, default launch) for 20 steps
+    against the oracle on the whole field."""
+    c = W.config_cylinder(1024, 2048)
+    g = Solver(c.params, storage="fp32")
+    g.init_fields(c.fields)
+    g.step(20)
+    o = oracle.Oracle(c.params)
+    o.init_fields(c.fields)
+    o.step(20)
+    got, want = g.fields(), o.fields()
+    for q in (1, 2, 3, 4):
+        assert _rel_l2(got[q], want[q]) < 1e-5, (q, _rel_l2(got[q], want[q]))
+    dg, do = g.diag(), o.diag()
+    assert dg["nu_avg"] == pytest.approx(do["nu_avg"], rel=1e-4)
+
+
+def test_invalid_parameters_are_rejected_on_device_path():
+    from paper_1806_10241_gb300._abi import LBError
+    p = cylinder_axis(8, 8)
+    p["omega_hi"] = 2.5
+    with pytest.raises(LBError):
+        Solver(p, storage="fp32")
