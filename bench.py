@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused axisymmetric cascaded LB step on GB300.
+
+Default workload: the swirling heated cylinder on a 1024 x 2048 meridian
+grid (H/R = 2, lid speed 0.05, Re = 1000, Ra = 1e5, Pr = 0.7), FP32.  A
+"step" is one time step of the whole method (stream + sources + three
+cascaded collisions + boundaries) over the lattice.  The metric is MLUPS
+(million node updates per second, each update covering f, g and h).
+
+  python bench.py [--gpus N --steps K --warmup W] [--storage fp32|fp16|bf16|fp64]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+With N > 1 (torchrun) every rank advances its own replica of the lattice
+(the method has no exchange between independent solves): weak scaling, one
+barrier and a max over ranks around the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (3-field node updates/s) & HBM roofline fraction; served solves/s, p99"
+BYTES_PER_NODE = {"fp64": 304, "fp32": 152, "bf16": 76, "fp16": 76}
+DTYPE = {"fp64": "f64", "fp32": "f32", "bf16": "f32 (bf16 storage)", "fp16": "f32 (fp16 storage)"}
+PROFILE_JSON = os.path.join(ROOT, "profiles", "roofline_counters.json")
+
+
+def workload_desc(nr, nz, storage):
+    return (f"swirling heated cylinder {nr}x{nz} (H/R=2, lid u=0.05, Re=1000, Ra=1e5, Pr=0.7), "
+            f"{storage} storage")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("lb_kernels.cu", "lb_internal.h"):
+        with open(os.path.join(ROOT, "paper_1806_10241_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def counters_for(key):
+    """Per-launch DRAM traffic from the committed ncu summary, only while the
+    kernel source still matches the one the counters were taken on."""
+    try:
+        with open(PROFILE_JSON) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(key)
+    if not e or e.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---- clocks -------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms in the background; keeps timestamps so
+    the timed window can be cut out afterwards."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self, t0, t1):
+        win = [s for t, s in self.samples if t0 - 0.1 <= t <= t1 + 0.1]
+        if not win and self.samples:  # short timed region: nearest samples
+            mid = 0.5 * (t0 + t1)
+            win = [min(self.samples, key=lambda ts: abs(ts[0] - mid))[1]]
+        if not win:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = sorted(v for v in (num(s[1]) for s in win) if v is not None)
+        smax = max((num(s[2]) or 0) for s in win)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in win for k in range(4)
+                          if len(s) > 5 + k and s[5 + k].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(win), "power_w_max": max((num(s[3]) or 0) for s in win)}
+
+
+# ---- the CPU oracle ---------------------------------------------------------------
+
+def oracle_mlups(nr, nz_full, budget_s, max_rows=None):
+    """Time the FP64 oracle on the host cores on a cylinder of nr columns and
+    as many rows of the same workload as fit the budget (one step at least)."""
+    import oracle
+    from paper_1806_10241_gb300 import workloads as W
+    oracle.build()
+    threads = oracle.get_threads()
+    rows = min(nz_full, max(8, 64))
+    c = W.config_cylinder(nr, rows)
+    o = oracle.Oracle(c.params)
+    o.init_fields(c.fields)
+    t = time.perf_counter()
+    o.step(1)
+    dt = max(time.perf_counter() - t, 1e-6)
+    rate = nr * rows / dt
+    steps = max(1, int(budget_s * rate / (nr * rows)))
+    if max_rows:
+        steps = min(steps, max_rows)
+    t = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t
+    return {"value": round(nr * rows * steps / dt / 1e6, 3), "unit": "MLUPS", "cores": threads,
+            "kind": "oracle",
+            "sample": f"FP64 oracle, {steps} steps of a {nr}x{rows} slab of the {nr}x{nz_full} "
+                      f"cylinder workload (same per-node work), {threads} OpenMP threads, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores, K steps after W
+    warm-up steps, each step a bounded slab of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1806_10241_gb300 import workloads as W
+    oracle.build()
+    nr, nz = args.nr, args.nz
+    # size the slab so the whole run ends in about two minutes
+    probe = W.config_cylinder(nr, 16)
+    o = oracle.Oracle(probe.params)
+    o.init_fields(probe.fields)
+    t = time.perf_counter()
+    o.step(2)
+    rate = 2 * nr * 16 / max(time.perf_counter() - t, 1e-6)  # node updates / s
+    total = args.steps + args.warmup
+    rows = int(max(4, min(nz, 120.0 * rate / (total * nr))))
+    c = W.config_cylinder(nr, rows)
+    o = oracle.Oracle(c.params)
+    o.init_fields(c.fields)
+    o.step(args.warmup)
+    t = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t
+    v = nr * rows * args.steps / dt / 1e6
+    threads = oracle.get_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * dt / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(nr, nz, "fp64") + f" -- slab {nr}x{rows} per step",
+                       "nr": nr, "nz": nz, "slab_rows": rows, "parallelism": "replicas"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                             "sample": f"{args.steps} steps of a {nr}x{rows} slab after {args.warmup} "
+                                       f"warm-up steps, {threads} OpenMP threads"},
+            "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- the GPU arm ----------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
+    ap.add_argument("--nr", type=int, default=1024)
+    ap.add_argument("--nz", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1806_10241_gb300 import workloads as W
+    from paper_1806_10241_gb300.solver import Solver
+
+    case = W.config_cylinder(args.nr, args.nz)
+    nodes = case.nr * case.nz
+    g = Solver(case.params, storage=args.storage, device=dev)
+    stream = g.stream
+    g.init_fields(case.fields)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    g.step(args.warmup)
+    barrier()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    gpu_index = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.6)
+
+    # device-timed region: K steps, one fused kernel each, inputs resident
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0 = time.time()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        g.step(args.steps)
+        e1.record(stream)
+    barrier()
+    t1 = time.time()
+    ms = e0.elapsed_time(e1)
+    clocks.stop()
+    if dist:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_per_step = ms / args.steps
+    value = world * nodes * args.steps / (ms * 1e3)  # MLUPS, whole job
+    d = g.diag()
+
+    # end to end through the C ABI with host buffers: upload the initial
+    # fields from pinned memory, K steps, download the fields
+    host_in = torch.from_numpy(np.ascontiguousarray(case.fields)).pin_memory()
+    host_out = torch.empty((5, case.nz, case.nr), dtype=torch.float64).pin_memory()
+    ge = Solver(case.params, storage=args.storage, device=dev)
+    e_steps = min(args.steps, 2000)
+    barrier()
+    t = time.perf_counter()
+    ge.init_fields(host_in.numpy())
+    ge.step(e_steps)
+    ge.fields(out=host_out.numpy())
+    barrier()
+    e2e_s = time.perf_counter() - t
+    if dist:
+        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": round(world * nodes * e_steps / e2e_s / 1e6, 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": int(host_in.numel() * 8 / e_steps),
+           "d2h_bytes_per_step": int(host_out.numel() * 8 / e_steps),
+           "steps": e_steps,
+           "what": "lb_init_fields (pinned host fields) + lb_step + lb_get_fields to host"}
+    del ge
+
+    peaks, peak_kind = measured_peaks()
+    bpn = BYTES_PER_NODE[args.storage]
+    achieved = bpn * nodes / (ms_per_step * 1e-3) / 1e9  # GB/s of one launch
+    peak = float(peaks["hbm_gbs"])
+    key = f"k_step_{args.storage}_{case.nr}x{case.nz}"
+    traffic = counters_for(key)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_node": bpn, "kernel": "k_step (fused stream+source+collide)"}
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.storage], "data": "synthetic",
+            "config": {"workload": workload_desc(case.nr, case.nz, args.storage), "nr": case.nr,
+                       "nz": case.nz, "storage": args.storage, "parallelism": "replicas",
+                       "l2": "inputs larger than L2 (working set %.0f MB)" % (2 * 19 * nodes *
+                                                                          bpn / 38 / 1e6)},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clocks.summary(t0, t1),
+            "diag": {"nu_avg": d["nu_avg"], "mass": d["mass"], "status": d["status"]}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_mlups(case.nr, case.nz, args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -89,8 +89,12 @@ class Solver:
     def step(self, n: int = 1) -> None:
         self._check(self.L.lb_step(self.ctx, int(n)))
 
-    def fields(self) -> np.ndarray:
-        a = np.empty((5, self.nz, self.nr), np.float64)
+    def fields(self, out: np.ndarray | None = None) -> np.ndarray:
+        """[5, nz, nr] rho, u_x, u_y, u_theta, T; `out` may be a (pinned)
+        float64 array of that shape to receive them."""
+        a = np.empty((5, self.nz, self.nr), np.float64) if out is None else out
+        if a.shape != (5, self.nz, self.nr) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a C-contiguous float64 array of shape (5, nz, nr)")
         self._check(self.L.lb_get_fields(self.ctx, _dptr(a)))
         return a
 
