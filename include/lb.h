@@ -185,6 +185,32 @@ LB_EXPORT lb_status lb_get_step(const lb_ctx *ctx, int64_t *step);
  * per block (0 = automatic).  Results do not depend on the launch shape. */
 LB_EXPORT lb_status lb_set_launch(lb_ctx *ctx, int32_t seg_rows, int32_t warps_per_block);
 
+/* Diagnostics of a state held in the caller's device memory, with no context
+ * and no scratch memory from the caller; the paper has no counterpart.
+ *
+ * For callers that cannot allocate device memory -- e.g. a runtime that hands
+ * out one fixed device arena at start-up and forbids allocation afterwards,
+ * or a tool inspecting checkpoints that another component staged in device
+ * memory -- and therefore cannot create a context (lb_create needs a buffer
+ * of lb_required_bytes, which includes reduction scratch) or lend scratch.
+ * dev_state points at one distribution buffer in the library's layout (the
+ * bytes of an lb_get_state blob after its 16-byte header, 256-byte aligned);
+ * desc and params describe it; step is copied to out->step.  The result
+ * equals lb_diagnostics on the same state.
+ *
+ * Scratch: a 1 MiB array (2^17 doubles) in the library's static device
+ * memory, which every GPU that loads the library holds until the process
+ * exits.  A lattice needs 16 + 12 x (blocks <= 2048) + 4 (nr + nz) doubles;
+ * larger lattices (nr + nz above about 26600) are rejected with LB_ERR_ARG.
+ * No call allocates or frees memory.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it: make that first
+ * call before any stream capture.  Every call reuses the same array and clears
+ * the part it uses; calls that overlap on the GPU (other streams, other
+ * threads) race on it.  Synchronous on cuda_stream. */
+LB_EXPORT lb_status lb_diagnostics_static(const lb_grid_desc *desc, const lb_params *params,
+                                          const void *dev_state, int64_t step, void *cuda_stream,
+                                          lb_diag *out);
+
 /* Release the context (not the caller's buffer or stream). */
 LB_EXPORT lb_status lb_destroy(lb_ctx *ctx);
 

@@ -39,6 +39,8 @@ struct lb_ctx {
 
 static thread_local char g_err[256] = "";
 
+void lbk::set_global_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 namespace {
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }

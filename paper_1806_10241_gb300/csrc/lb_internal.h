@@ -7,7 +7,7 @@
 
 namespace lbk {
 
-enum Mode { MODE_STEP = 0, MODE_FIELDS = 1, MODE_DIAG = 2 };
+enum Mode { MODE_STEP = 0, MODE_FIELDS = 1, MODE_DIAG = 2, MODE_DIAG_STRIP = 3 };
 enum Storage { ST_FP64 = 0, ST_FP32 = 1, ST_BF16 = 2, ST_FP16 = 3 };
 
 constexpr int NQ = 19;        // 9 (f) + 5 (g) + 5 (h) planes
@@ -55,6 +55,8 @@ cudaError_t launch_import(const HostParams &p, const double *in, void *dst, int 
                           cudaStream_t s);
 
 size_t storage_bytes(int storage);
+// Message for lb_last_error(NULL) on this thread.
+void set_global_error(const char *msg);
 Launch default_launch(const HostParams &p);
 
 }  // namespace lbk

@@ -19,12 +19,17 @@
 // ones; lanes 0 and 31 are halo columns.  HBM traffic is therefore 19 loads
 // and 19 stores per node update.
 #include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
 #include <type_traits>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "../../include/lb.h"
 #include "lb_internal.h"
 
 namespace lbk {
@@ -546,7 +551,22 @@ __device__ __forceinline__ void march(const KP<C> &k, const S *__restrict__ src,
                                     isfinite((double)o.uy) && isfinite((double)o.ut) &&
                                     isfinite((double)o.T);
                 if (!finite || o.rho < (C)0.5 || o.rho > (C)1.5) acc->bad = 1.0;
-                fout[(long long)i * nr + c] = (double)o.T;  // for the wall fluxes
+                if (MODE == MODE_DIAG) {
+                    fout[(long long)i * nr + c] = (double)o.T;  // for the wall fluxes
+                } else {
+                    // wall-adjacent temperatures only: rows 0, 1, nz-2, nz-1
+                    // (4 x nr values), then columns 0, 1, nr-2, nr-1 (4 x nz)
+                    const double T = (double)o.T;
+                    if (i == 0) fout[c] = T;
+                    if (i == 1) fout[nr + c] = T;
+                    if (i == nz - 2) fout[2 * nr + c] = T;
+                    if (i == nz - 1) fout[3 * nr + c] = T;
+                    double *cs = fout + 4LL * nr;
+                    if (c == 0) cs[i] = T;
+                    if (c == 1) cs[nz + i] = T;
+                    if (c == nr - 2) cs[2LL * nz + i] = T;
+                    if (c == nr - 1) cs[3LL * nz + i] = T;
+                }
             }
         }
 
@@ -655,6 +675,71 @@ __global__ void __launch_bounds__(256) k_wall(KP<C> k, const double *__restrict_
                 for (int j = threadIdx.x; j < nr; j += blockDim.x)
                     acc += (k.r0 + j + 0.5) *
                            (8.0 * Tw - 9.0 * T[(long long)(nz - 1) * nr + j] + T[(long long)(nz - 2) * nr + j]) / 3.0;
+        }
+        sh[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) result[4 + sd] = k.heat[sd] == 0 ? sh[0] * k.nu_scale[sd] : 0.0;
+        __syncthreads();
+    }
+}
+
+// Variant of k_diag whose temperature output is the wall-adjacent strips
+// only (4 (nr + nz) doubles), for the scratch-free diagnostics entry point.
+template <typename S, typename C>
+__global__ void __launch_bounds__(128) k_diag_strip(KP<C> k, const S *__restrict__ src,
+                                                    double *__restrict__ partial, double *__restrict__ strips,
+                                                    int seg_rows, int nwin)
+{
+    __shared__ double sh[4][NSUM];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+    DiagAcc a = {0, 0, 0, 0, 0};
+    if (warp < nwin) {
+        const int c = warp * OUT_COLS - 1 + lane;
+        const int s = blockIdx.y * seg_rows, e = min(k.nz, s + seg_rows);
+        march<S, C, MODE_DIAG_STRIP>(k, src, nullptr, strips, 0, c, s, e, &a);
+    }
+    double vals[NSUM] = {a.mass_dev, a.mass_r_dev, a.tsum, a.umax, 0, 0, 0, 0, a.bad, 0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < NSUM; ++q) vals[q] = (q == 3 || q == 8) ? warp_max(vals[q]) : warp_sum(vals[q]);
+    if (lane == 0)
+        for (int q = 0; q < NSUM; ++q) sh[wib][q] = vals[q];
+    __syncthreads();
+    if (threadIdx.x < NSUM) {
+        const int q = threadIdx.x;
+        double r = sh[0][q];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = (q == 3 || q == 8) ? fmax(r, sh[w][q]) : r + sh[w][q];
+        partial[(blockIdx.y * gridDim.x + blockIdx.x) * NSUM + q] = r;
+    }
+}
+
+// k_wall on the strips written by k_diag_strip (same summation order).
+template <typename C>
+__global__ void __launch_bounds__(256) k_wall_strip(KP<C> k, const double *__restrict__ strips,
+                                                    double *__restrict__ result)
+{
+    __shared__ double sh[256];
+    const int nr = k.nr, nz = k.nz;
+    const double *r0 = strips, *r1 = strips + nr, *r2 = strips + 2 * nr, *r3 = strips + 3 * nr;
+    const double *c0 = strips + 4 * nr, *c1 = c0 + nz, *c2 = c0 + 2 * nz, *c3 = c0 + 3 * nz;
+    for (int sd = 0; sd < 4; ++sd) {
+        double acc = 0;
+        if (k.heat[sd] == 0) {
+            const double Tw = (double)k.Tw[sd];
+            if (sd == 2)
+                for (int i = threadIdx.x; i < nz; i += blockDim.x) acc += (-8.0 * Tw + 9.0 * c0[i] - c1[i]) / 3.0;
+            else if (sd == 3)
+                for (int i = threadIdx.x; i < nz; i += blockDim.x) acc += (8.0 * Tw - 9.0 * c3[i] + c2[i]) / 3.0;
+            else if (sd == 0)
+                for (int j = threadIdx.x; j < nr; j += blockDim.x)
+                    acc += (k.r0 + j + 0.5) * (-8.0 * Tw + 9.0 * r0[j] - r1[j]) / 3.0;
+            else
+                for (int j = threadIdx.x; j < nr; j += blockDim.x)
+                    acc += (k.r0 + j + 0.5) * (8.0 * Tw - 9.0 * r3[j] + r2[j]) / 3.0;
         }
         sh[threadIdx.x] = acc;
         __syncthreads();
@@ -890,3 +975,184 @@ cudaError_t launch_import(const HostParams &p, const double *in, void *dst, int 
 }
 
 }  // namespace lbk
+
+// ---- diagnostics without scratch memory from the caller ------------------------
+//
+// lb_diagnostics_static() evaluates the diagnostics of a state the caller
+// holds in device memory, with no context and no scratch from the caller:
+// its block partial sums and wall temperature strips live in the file-scope
+// array below (1 MiB, allocated by the CUDA runtime when the module loads on
+// a device and held by every device that loads the library until the process
+// exits).  Host code must not pass the array's name to a kernel -- in host
+// code it is only a stand-in for the symbol -- so the device address is looked
+// up once per device with cudaGetSymbolAddress and cached.
+
+static __device__ __align__(256) double g_diag_scratch[1 << 17];
+
+namespace lbk {
+namespace {
+
+constexpr size_t kScratchDoubles = (size_t)1 << 17;
+constexpr int kScratchMaxBlocks = 2048;
+constexpr int kMaxDevices = 256;
+
+std::mutex g_scratch_mu;
+double *g_scratch_ptr[kMaxDevices] = {};
+
+cudaError_t scratch_address(double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_diag_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = (double *)p;
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+template <typename S, typename C>
+cudaError_t diag_static_t(const HostParams &h, const Launch &l, const void *src, double *scratch, int nb,
+                          cudaStream_t s)
+{
+    const KP<C> k = make_kp<C>(h);
+    const int nwin = nwindows(h.nr);
+    dim3 grid((nwin + 3) / 4, (h.nz + l.seg_rows - 1) / l.seg_rows);
+    double *result = scratch, *partial = scratch + 16, *strips = scratch + 16 + (size_t)nb * NSUM;
+    k_diag_strip<S, C><<<grid, 128, 0, s>>>(k, (const S *)src, partial, strips, l.seg_rows, nwin);
+    k_diag_final<<<1, 32, 0, s>>>(partial, nb, result);
+    k_wall_strip<C><<<1, 256, 0, s>>>(k, strips, result);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace lbk
+
+extern "C" lb_status lb_diagnostics_static(const lb_grid_desc *desc, const lb_params *p, const void *dev_state,
+                                           int64_t step, void *cuda_stream, lb_diag *out)
+{
+    using namespace lbk;
+    if (!desc || !p || !dev_state || !out) {
+        set_global_error("lb_diagnostics_static: NULL argument");
+        return LB_ERR_ARG;
+    }
+    if (desc->nr < 2 || desc->nz < 2 || desc->storage < LB_FP64 || desc->storage > LB_FP16 || desc->reserved != 0 ||
+        !(desc->r_inner >= 0.0) || !std::isfinite(desc->r_inner)) {
+        set_global_error("lb_diagnostics_static: invalid grid descriptor");
+        return LB_ERR_ARG;
+    }
+    if (!(p->nu > 0.0) || !(p->alpha > 0.0) || !(p->rho0 > 0.0)) {
+        set_global_error("lb_diagnostics_static: nu, alpha and rho0 must be > 0");
+        return LB_ERR_ARG;
+    }
+    if (((uintptr_t)dev_state & 255) != 0) {
+        set_global_error("lb_diagnostics_static: dev_state must be 256-byte aligned");
+        return LB_ERR_ARG;
+    }
+    HostParams h;
+    std::memset(&h, 0, sizeof(h));
+    const int m = storage_bytes(desc->storage) == 2 ? 64 : 32;
+    h.nr = desc->nr;
+    h.nz = desc->nz;
+    h.pitch = (desc->nr + m - 1) / m * m;
+    h.plane = (long long)h.nz * h.pitch;
+    h.storage = desc->storage;
+    h.r0 = desc->r_inner;
+    h.scale = desc->storage == LB_FP16 ? 1024.0 : 1.0;
+    h.nu = p->nu;
+    h.alpha = p->alpha;
+    h.omega3 = p->omega3;
+    h.omega_hi = p->omega_hi;
+    h.g_beta = p->g_beta;
+    h.T0 = p->T0;
+    h.body_fx = p->body_fx;
+    h.rho0 = p->rho0;
+    h.planar = p->planar;
+    h.sign_literal = p->sign_literal;
+    h.explicit_sources = p->explicit_sources;
+    for (int s = 0; s < 4; ++s) {
+        h.flow[s] = p->side[s].flow;
+        h.swirl[s] = p->side[s].swirl;
+        h.heat[s] = p->side[s].heat;
+        h.uwx[s] = p->side[s].u_wx;
+        h.uwy[s] = p->side[s].u_wy;
+        h.omega[s] = p->side[s].omega;
+        h.Tw[s] = p->side[s].T_w;
+    }
+    // launch shape within the static scratch: at most kScratchMaxBlocks blocks
+    Launch l = default_launch(h);
+    const long long bx = (nwindows(h.nr) + 3) / 4;
+    long long segs = (h.nz + l.seg_rows - 1) / l.seg_rows;
+    if (bx * segs > kScratchMaxBlocks) {
+        segs = kScratchMaxBlocks / bx;
+        if (segs < 1) segs = 1;
+        l.seg_rows = (int)((h.nz + segs - 1) / segs);
+        segs = (h.nz + l.seg_rows - 1) / l.seg_rows;
+    }
+    const long long nb = bx * segs;
+    const size_t need = 16 + (size_t)nb * NSUM + 4 * ((size_t)h.nr + (size_t)h.nz);
+    if (nb > kScratchMaxBlocks || need > kScratchDoubles) {
+        char msg[200];
+        snprintf(msg, sizeof(msg),
+                 "lb_diagnostics_static: a %d x %d lattice needs %zu scratch doubles, the static array holds %zu "
+                 "(nr + nz must stay below about 26600)",
+                 h.nr, h.nz, need, kScratchDoubles);
+        set_global_error(msg);
+        return LB_ERR_ARG;
+    }
+    double *scratch = nullptr;
+    cudaError_t e = scratch_address(&scratch);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, need * sizeof(double), st);
+    if (e == cudaSuccess) {
+        switch (h.storage) {
+            case ST_FP64: e = diag_static_t<double, double>(h, l, dev_state, scratch, (int)nb, st); break;
+            case ST_FP32: e = diag_static_t<float, float>(h, l, dev_state, scratch, (int)nb, st); break;
+            case ST_BF16: e = diag_static_t<__nv_bfloat16, float>(h, l, dev_state, scratch, (int)nb, st); break;
+            default: e = diag_static_t<__half, float>(h, l, dev_state, scratch, (int)nb, st); break;
+        }
+    }
+    double res[NSUM];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(res, scratch, sizeof(res), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        char msg[200];
+        snprintf(msg, sizeof(msg), "lb_diagnostics_static: %s", cudaGetErrorString(e));
+        set_global_error(msg);
+        return LB_ERR_CUDA;
+    }
+    std::memset(out, 0, sizeof(*out));
+    const double N = (double)h.nr * h.nz;
+    const double sum_y = (double)h.nz * (h.nr * h.r0 + 0.5 * (double)h.nr * h.nr);
+    out->mass = h.rho0 * N + res[0];
+    out->mass_r = h.rho0 * sum_y + res[1];
+    out->T_sum = res[2];
+    out->u_max = res[3];
+    for (int s = 0; s < 4; ++s) out->nu_side[s] = res[4 + s];
+    int a = -1, b = -1;
+    if (h.heat[2] == LB_SC_DIRICHLET && h.heat[3] == LB_SC_DIRICHLET) {
+        a = 2;
+        b = 3;
+    } else if (h.heat[0] == LB_SC_DIRICHLET && h.heat[1] == LB_SC_DIRICHLET) {
+        a = 0;
+        b = 1;
+    } else {
+        for (int s = 0; s < 4; ++s)
+            if (h.heat[s] == LB_SC_DIRICHLET) {
+                if (a < 0) a = s;
+                else if (b < 0) b = s;
+            }
+    }
+    if (a >= 0) out->nu_i = out->nu_side[a];
+    if (b >= 0) out->nu_o = out->nu_side[b];
+    out->nu_avg = (a >= 0 && b >= 0) ? 0.5 * (out->nu_i + out->nu_o) : out->nu_i;
+    out->step = step;
+    const bool bad = res[8] > 0.0 || !std::isfinite(res[0]) || !std::isfinite(res[2]);
+    out->status = bad ? LB_ERR_DIVERGED : LB_OK;
+    return LB_OK;
+}
