@@ -132,6 +132,23 @@ class ClockSampler:
                 "samples": len(win), "power_w_max": max((num(s[3]) or 0) for s in win)}
 
 
+# ---- multi-rank timing ---------------------------------------------------------------
+
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The largest value over all ranks (the job's time is its slowest rank's)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world: int, nodes: int, steps: int, ms: float) -> float:
+    """Whole-job MLUPS: every rank advances its own replica of `nodes` nodes."""
+    return world * nodes * steps / (ms * 1e3)
+
+
 # ---- the CPU oracle ---------------------------------------------------------------
 
 def oracle_mlups(nr, nz_full, budget_s, max_rows=None):
@@ -279,12 +296,9 @@ def main():
     t1 = time.time()
     ms = e0.elapsed_time(e1)
     clocks.stop()
-    if dist:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dist, dev)
     ms_per_step = ms / args.steps
-    value = world * nodes * args.steps / (ms * 1e3)  # MLUPS, whole job
+    value = job_mlups(world, nodes, args.steps, ms)  # MLUPS, whole job
     d = g.diag()
 
     # end to end through the C ABI with host buffers: upload the initial
@@ -299,11 +313,7 @@ def main():
     ge.step(e_steps)
     ge.fields(out=host_out.numpy())
     barrier()
-    e2e_s = time.perf_counter() - t
-    if dist:
-        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t, dist, dev)
     e2e = {"value": round(world * nodes * e_steps / e2e_s / 1e6, 1), "unit": "MLUPS",
            "h2d_bytes_per_step": int(host_in.numel() * 8 / e_steps),
            "d2h_bytes_per_step": int(host_out.numel() * 8 / e_steps),

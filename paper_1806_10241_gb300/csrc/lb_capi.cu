@@ -274,7 +274,7 @@ lb_status lb_step(lb_ctx *ctx, int32_t nsteps)
     if (nsteps < 0) return fail(ctx, LB_ERR_ARG, "nsteps < 0");
     for (int32_t t = 0; t < nsteps; ++t) {
         cudaError_t e = lbk::launch_step(ctx->hp, ctx->launch, ctx->dist[ctx->cur], ctx->dist[1 - ctx->cur],
-                                         ctx->stream);
+                                         (unsigned long long)ctx->step, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
         ctx->cur ^= 1;
         ctx->step += 1;

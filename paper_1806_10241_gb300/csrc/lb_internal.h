@@ -33,9 +33,10 @@ struct Launch {
     int warps_per_block;
 };
 
-// One time step src -> dst.
+// One time step src -> dst; `step` seeds the stochastic rounding of 16-bit
+// storage.
 cudaError_t launch_step(const HostParams &p, const Launch &l, const void *src, void *dst,
-                        cudaStream_t s);
+                        unsigned long long step, cudaStream_t s);
 // Pre-collision fields of rows [row0, row1) into out[5][row1-row0][nr] (double).
 cudaError_t launch_fields(const HostParams &p, const Launch &l, const void *src, double *out,
                           int row0, int row1, cudaStream_t s);

@@ -38,26 +38,43 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int OUT_COLS = 30;  // columns updated per warp
+#ifndef LB_MARCH_UNROLL
+#define LB_MARCH_UNROLL 2
+#endif
+constexpr int kMarchUnroll = LB_MARCH_UNROLL;  // rows per unrolled march iteration
 
 // ---- storage conversions ------------------------------------------------
 
 template <typename S, typename C> struct Cvt;
 template <> struct Cvt<double, double> {
+    static __device__ __forceinline__ double cv(double x) { return x; }
     static __device__ __forceinline__ double ld(const double *p) { return *p; }
     static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
 };
 template <> struct Cvt<float, float> {
+    static __device__ __forceinline__ float cv(float x) { return x; }
     static __device__ __forceinline__ float ld(const float *p) { return *p; }
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 };
 template <> struct Cvt<__nv_bfloat16, float> {
+    static __device__ __forceinline__ float cv(__nv_bfloat16 x) { return __bfloat162float(x); }
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 template <> struct Cvt<__half, float> {
+    static __device__ __forceinline__ float cv(__half x) { return __half2float(x); }
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 };
+
+// 1/x: the hardware reciprocal for FP32 (|error| <= 2 ulp, far inside the
+// FP32 parity tolerances), a correctly rounded division for FP64
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
+// FP16 storage is scaled (deviations x 1024, away from the subnormal range);
+// the other storage types are not, and skip the multiplications.
+template <typename S> struct Scaled { static constexpr bool value = std::is_same<S, __half>::value; };
 
 // ---- kernel parameters in the compute type --------------------------------
 
@@ -137,16 +154,23 @@ template <typename C> struct PM {  // macroscopic fields of the stored state
     C rd, ux, uy, ut, T;
 };
 
-template <typename C> __device__ __forceinline__ PM<C> moments(const C v[NQ], const KP<C> &k)
+template <typename S, typename C> __device__ __forceinline__ PM<C> moments(const C v[NQ], const KP<C> &k)
 {
     // rho = rho0 + sum f_dev, j = sum f_dev e, psi = sum g, T = T0 + sum h_dev
-    const C is = k.inv_scale;
-    const C rd = (v[0] + v[1] + v[2] + v[3] + v[4] + v[5] + v[6] + v[7] + v[8]) * is;
-    const C jx = (v[1] - v[3] + v[5] - v[6] - v[7] + v[8]) * is;
-    const C jy = (v[2] - v[4] + v[5] + v[6] - v[7] - v[8]) * is;
-    const C ps = (v[9] + v[10] + v[11] + v[12] + v[13]) * is;
-    const C td = (v[14] + v[15] + v[16] + v[17] + v[18]) * is;
-    const C ir = (C)1 / (k.rho0 + rd);
+    C rd = v[0] + v[1] + v[2] + v[3] + v[4] + v[5] + v[6] + v[7] + v[8];
+    C jx = v[1] - v[3] + v[5] - v[6] - v[7] + v[8];
+    C jy = v[2] - v[4] + v[5] + v[6] - v[7] - v[8];
+    C ps = v[9] + v[10] + v[11] + v[12] + v[13];
+    C td = v[14] + v[15] + v[16] + v[17] + v[18];
+    if (Scaled<S>::value) {
+        const C is = k.inv_scale;
+        rd *= is;
+        jx *= is;
+        jy *= is;
+        ps *= is;
+        td *= is;
+    }
+    const C ir = rcp(k.rho0 + rd);
     PM<C> m;
     m.rd = rd;
     m.ux = jx * ir;
@@ -196,6 +220,15 @@ __device__ __forceinline__ void load_row(const S *__restrict__ src, const KP<C> 
     for (int q = 0; q < NQ; ++q) v[q] = Cvt<S, C>::ld(p + q * k.plane);
 }
 
+// raw (unconverted) loads of one row, issued ahead of their use
+template <typename S, typename C>
+__device__ __forceinline__ void load_raw(const S *__restrict__ src, const KP<C> &k, int row, int col, S r[NQ])
+{
+    const S *p = src + (long long)row * k.pitch + col;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) r[q] = p[q * k.plane];
+}
+
 template <typename S, typename C>
 __device__ __forceinline__ C own(const S *__restrict__ src, const KP<C> &k, int q, int row, int col)
 {
@@ -239,34 +272,44 @@ __device__ __forceinline__ void update_node(const KP<C> &k, C y, C iy, C fv[9], 
     const C pso = gv[0] + gv[1] + gv[2] + gv[3] + gv[4];
     const C tdo = hv[0] + hv[1] + hv[2] + hv[3] + hv[4];
 
-    // sources (Eq. 4a-4c, 5, 7, 9) at the pre-collision state, two sweeps
+    // sources (Eq. 4a-4c, 5, 7, 9) at the pre-collision state, two sweeps.
+    // Written per unit of the swept state (rd, j, psi, td): with mu = rho nu,
+    //   F_x^A = -j_x u_y / y + rho nu (d_x u_y + d_y u_x) / y
+    //   F_y^A = psi^2 / (rho y) - j_y u_y / y + rho 2 nu d_y u_y / y - 2 nu j_y / y^2
+    //   S_psi = -2 u_y psi / y + rho nu d_y u_theta / y - nu psi / y^2
+    //   S_phi = -u_y T / y + alpha d_y T / y
+    // so the gradient factors are formed once per node.
     C rd = rdo, jx = jxo, jy = jyo, ps = pso, td = tdo;
     C MA = 0, Fx = 0, Fy = 0, Sps = 0, Sph = 0;
+    const bool geo = !k.planar;
+    const C Gx = geo ? k.nu * (dxuy + dyux) * iy : (C)0;
+    const C Gy = geo ? (C)2 * k.nu * dyuy * iy : (C)0;
+    const C Gw = geo ? k.nu * dyut * iy : (C)0;
+    const C Gt = geo ? k.alpha * dyT * iy : (C)0;
+    const C iy2nu = geo ? k.nu * iy * iy : (C)0;
+    const C gy = geo ? iy : (C)0;
+    const C Fb = k.rho0 * k.gbeta;
     const int sweeps = k.explicit_src ? 1 : 2;
     for (int sw = 0; sw < sweeps; ++sw) {
-        const C r = k.rho0 + rd, ir = (C)1 / r;
-        const C ux = jx * ir, uy = jy * ir, ph = k.T0 + td;
-        C MAs = 0, FAx = 0, FAy = 0;
-        Sps = 0;
-        Sph = 0;
-        if (!k.planar) {
-            const C mu = r * k.nu;
-            MAs = -jy * iy;
-            FAx = -jx * uy * iy + mu * (dxuy + dyux) * iy;
-            FAy = ps * ps * ir * iy - jy * uy * iy + (C)2 * mu * dyuy * iy - (C)2 * mu * uy * iy * iy;
-            Sps = (C)-2 * uy * ps * iy + mu * iy * dyut - k.nu * ps * iy * iy;
-            Sph = -uy * ph * iy + k.alpha * iy * dyT;
-        }
-        Fx = FAx + k.rho0 * k.gbeta * td + k.bfx;
+        const C r = k.rho0 + rd, ir = rcp(r);
+        const C uyy = jy * ir * gy;  // u_y / y
+        const C ph = k.T0 + td;
+        const C FAx = -jx * uyy + r * Gx;
+        const C FAy = (ps * ps - jy * jy) * ir * gy + r * Gy - (C)2 * jy * iy2nu;
+        Sps = (C)-2 * uyy * ps + r * Gw - iy2nu * ps;
+        Sph = -uyy * ph + Gt;
+        Fx = FAx + Fb * td + k.bfx;
         Fy = FAy;
         jx = jxo + (C)0.5 * Fx;
         jy = jyo + (C)0.5 * Fy;
         ps = pso + (C)0.5 * Sps;
         td = tdo + (C)0.5 * Sph;
-        MA = (k.planar || k.explicit_src) ? MAs : -jy * iy;
+        // M^A = -j_y / y, from the newest momentum (from the output momentum
+        // in the single-evaluation mode)
+        MA = -(k.explicit_src ? jyo : jy) * gy;
         rd = rdo + (C)0.5 * MA;
     }
-    const C r = k.rho0 + rd, ir = (C)1 / r;
+    const C r = k.rho0 + rd, ir = rcp(r);
     const C ux = jx * ir, uy = jy * ir;
     const C phi = k.T0 + td;
     o.rho = r;
@@ -386,29 +429,39 @@ __device__ __forceinline__ void march(const KP<C> &k, const S *__restrict__ src,
         load_row<S, C>(src, k, rm, cl, v);
         C x0t[9], xpt[5];
         groups<C>(v, xm_prev, x0t, xpt);
-        uy_prev = moments<C>(v, k).uy;
+        uy_prev = moments<S, C>(v, k).uy;
         has_m = true;
     } else {
         has_m = false;
 #pragma unroll
         for (int q = 0; q < 5; ++q) xm_prev[q] = 0;
     }
+    // software pipeline: the raw values of row i+1 are loaded during the
+    // iteration for row i-1, so a row's DRAM latency overlaps the previous
+    // row's arithmetic
+    S nb[NQ];
+    if ((row_s + 1 < nz) || k.xper) load_raw<S, C>(src, k, row_s + 1 < nz ? row_s + 1 : 0, cl, nb);
     {
         load_row<S, C>(src, k, row_s, cl, v);
         C xpt[5];
         groups<C>(v, xm_cur, x0_cur, xpt);
-        pm_cur = moments<C>(v, k);
+        pm_cur = moments<S, C>(v, k);
     }
 
+#pragma unroll kMarchUnroll
     for (int i = row_s; i < row_e; ++i) {
         const bool has_p = (i + 1 < nz) || k.xper;
         C xp_n[5], x0_n[9], xm_n[5];
         PM<C> pm_n;
         if (has_p) {
-            const int rp = i + 1 < nz ? i + 1 : 0;
-            load_row<S, C>(src, k, rp, cl, v);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) v[q] = Cvt<S, C>::cv(nb[q]);
+        }
+        if (i + 1 < row_e && ((i + 2 < nz) || k.xper))
+            load_raw<S, C>(src, k, i + 2 < nz ? i + 2 : i + 2 - nz, cl, nb);
+        if (has_p) {
             groups<C>(v, xm_n, x0_n, xp_n);
-            pm_n = moments<C>(v, k);
+            pm_n = moments<S, C>(v, k);
         } else {
 #pragma unroll
             for (int q = 0; q < 5; ++q) xp_n[q] = xm_n[q] = 0;
@@ -474,12 +527,14 @@ __device__ __forceinline__ void march(const KP<C> &k, const S *__restrict__ src,
             gv[3] = scalar_bc<C>(k.swirl[sd], own<S, C>(src, k, G0 + 1, i, cl), wall_psi<C>(k, sd, y) * sc, true);
             hv[3] = scalar_bc<C>(k.heat[sd], own<S, C>(src, k, H0 + 1, i, cl), (k.Tw[sd] - k.T0) * sc, false);
         }
+        if (Scaled<S>::value) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) fv[q] *= is;
+            for (int q = 0; q < 9; ++q) fv[q] *= is;
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            gv[q] *= is;
-            hv[q] *= is;
+            for (int q = 0; q < 5; ++q) {
+                gv[q] *= is;
+                hv[q] *= is;
+            }
         }
 
         // central differences of the stored-state fields, with ghosts
@@ -522,12 +577,15 @@ __device__ __forceinline__ void march(const KP<C> &k, const S *__restrict__ src,
         if (MODE == MODE_STEP) {
             if (out_lane) {
                 S *p = dst + (long long)i * k.pitch + c;
+                const C m = Scaled<S>::value ? sc : (C)1;
 #pragma unroll
-                for (int q = 0; q < 9; ++q) Cvt<S, C>::st(p + q * k.plane, o.f[q] * sc);
+                for (int q = 0; q < 9; ++q) Cvt<S, C>::st(p + q * k.plane, Scaled<S>::value ? o.f[q] * m : o.f[q]);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) Cvt<S, C>::st(p + (G0 + q) * k.plane, o.g[q] * sc);
+                for (int q = 0; q < 5; ++q)
+                    Cvt<S, C>::st(p + (G0 + q) * k.plane, Scaled<S>::value ? o.g[q] * m : o.g[q]);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) Cvt<S, C>::st(p + (H0 + q) * k.plane, o.h[q] * sc);
+                for (int q = 0; q < 5; ++q)
+                    Cvt<S, C>::st(p + (H0 + q) * k.plane, Scaled<S>::value ? o.h[q] * m : o.h[q]);
             }
         } else if (MODE == MODE_FIELDS) {
             if (out_lane) {
@@ -584,9 +642,14 @@ __device__ __forceinline__ void march(const KP<C> &k, const S *__restrict__ src,
     }
 }
 
+#include "lb_pair.cuh"
+
+#ifndef LB_STEP_MAXREG
+#define LB_STEP_MAXREG 128
+#endif
 template <typename S, typename C>
-__global__ void __launch_bounds__(256) k_step(KP<C> k, const S *__restrict__ src, S *__restrict__ dst,
-                                              int seg_rows, int nwin)
+__device__ __forceinline__ void step_body(const KP<C> &k, const S *__restrict__ src, S *__restrict__ dst,
+                                          int seg_rows, int nwin)
 {
     const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (warp >= nwin) return;  // whole warps only
@@ -594,6 +657,38 @@ __global__ void __launch_bounds__(256) k_step(KP<C> k, const S *__restrict__ src
     const int s = blockIdx.y * seg_rows;
     const int e = min(k.nz, s + seg_rows);
     march<S, C, MODE_STEP>(k, src, dst, nullptr, 0, c, s, e, nullptr);
+}
+
+// FP32-compute step (FP32 / BF16 / FP16 storage): register cap for 24
+// resident warps per SM without spills
+template <typename S, typename C>
+__global__ void __maxnreg__(LB_STEP_MAXREG) k_step(KP<C> k, const S *__restrict__ src, S *__restrict__ dst,
+                                                   int seg_rows, int nwin)
+{
+    step_body<S, C>(k, src, dst, seg_rows, nwin);
+}
+
+// FP64 step: twice the registers per value
+template <typename S, typename C>
+__global__ void __maxnreg__(255) k_step64(KP<C> k, const S *__restrict__ src, S *__restrict__ dst,
+                                          int seg_rows, int nwin)
+{
+    step_body<S, C>(k, src, dst, seg_rows, nwin);
+}
+
+// FP32-compute step on column pairs (lb_pair.cuh): 64 aligned columns per warp
+#ifndef LB_STEP2_MAXREG
+#define LB_STEP2_MAXREG 168
+#endif
+template <typename S>
+__global__ void __maxnreg__(LB_STEP2_MAXREG) k_step2(KP<float> k, const S *__restrict__ src, S *__restrict__ dst,
+                                                     int seg_rows, int nwin2, uint32_t salt)
+{
+    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (warp >= nwin2) return;
+    const int s = blockIdx.y * seg_rows;
+    const int e = min(k.nz, s + seg_rows);
+    march2<S>(k, src, dst, warp * 64, s, e, salt);
 }
 
 template <typename S, typename C>
@@ -848,15 +943,34 @@ __global__ void k_import(HostParams h, const double *__restrict__ in, S *__restr
 
 int nwindows(int nr) { return (nr + OUT_COLS - 1) / OUT_COLS; }
 
+int nwindows2(int nr) { return (nr + 63) / 64; }
+
+uint32_t step_salt(unsigned long long step)
+{
+    // SplitMix64 finaliser of the step counter (random bits of the stochastic
+    // rounding differ from step to step)
+    unsigned long long z = step + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return (uint32_t)(z ^ (z >> 31));
+}
+
 template <typename S, typename C>
-cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *dst, cudaStream_t s)
+cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *dst, unsigned long long step,
+                   cudaStream_t s)
 {
     const KP<C> k = make_kp<C>(h);
-    const int nwin = nwindows(h.nr);
     const int wpb = l.warps_per_block;
     const int seg = l.seg_rows;
-    dim3 grid((nwin + wpb - 1) / wpb, (h.nz + seg - 1) / seg);
-    k_step<S, C><<<grid, 32 * wpb, 0, s>>>(k, (const S *)src, (S *)dst, seg, nwin);
+    if constexpr (std::is_same<C, double>::value) {
+        const int nwin = nwindows(h.nr);
+        dim3 grid((nwin + wpb - 1) / wpb, (h.nz + seg - 1) / seg);
+        k_step64<S, C><<<grid, 32 * wpb, 0, s>>>(k, (const S *)src, (S *)dst, seg, nwin);
+    } else {
+        const int nwin2 = nwindows2(h.nr);
+        dim3 grid((nwin2 + wpb - 1) / wpb, (h.nz + seg - 1) / seg);
+        k_step2<S><<<grid, 32 * wpb, 0, s>>>(k, (const S *)src, (S *)dst, seg, nwin2, step_salt(step));
+    }
     return cudaGetLastError();
 }
 
@@ -906,13 +1020,16 @@ Launch default_launch(const HostParams &p)
 {
     Launch l;
     l.warps_per_block = 4;
-    // aim for about 8 resident warps per SM-slot across 152 SMs
-    const int nwin = nwindows(p.nr);
-    const long long target_warps = 152LL * 24;
-    long long segs = (target_warps + nwin - 1) / nwin;
-    if (segs < 1) segs = 1;
-    int seg = (int)((p.nz + segs - 1) / segs);
-    if (seg < 8) seg = 8;
+    // 32-row segments (two halo rows per segment, 6 %), fewer when the
+    // lattice would otherwise leave SMs idle
+    const int nwin = p.storage == ST_FP64 ? nwindows(p.nr) : nwindows2(p.nr);
+    int seg = p.storage == ST_FP64 ? 32 : 8;
+    const long long warps = (long long)nwin * ((p.nz + seg - 1) / seg);
+    if (warps < 152LL * 16) {
+        const long long segs = (152LL * 16 + nwin - 1) / nwin;
+        seg = (int)((p.nz + segs - 1) / segs);
+        if (seg < 8) seg = 8;
+    }
     l.seg_rows = seg;
     return l;
 }
@@ -926,9 +1043,10 @@ Launch default_launch(const HostParams &p)
         default: return cudaErrorInvalidValue;                              \
     }
 
-cudaError_t launch_step(const HostParams &p, const Launch &l, const void *src, void *dst, cudaStream_t s)
+cudaError_t launch_step(const HostParams &p, const Launch &l, const void *src, void *dst, unsigned long long step,
+                        cudaStream_t s)
 {
-    DISPATCH(p, (step_t<S, C>(p, l, src, dst, s)));
+    DISPATCH(p, (step_t<S, C>(p, l, src, dst, step, s)));
 }
 
 cudaError_t launch_fields(const HostParams &p, const Launch &l, const void *src, double *out, int row0, int row1,

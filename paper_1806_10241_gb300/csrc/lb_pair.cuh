@@ -1,0 +1,634 @@
+// Two radial columns per lane (included by lb_kernels.cu inside its
+// anonymous namespace; FP32 arithmetic, FP32 / FP16 / BF16 storage).
+//
+// A warp owns 64 adjacent, 64-aligned columns: lane l holds columns
+// c0 + 2l ("x" of every pair) and c0 + 2l + 1 ("y").  Rows are read and
+// written as float2 / half2 pairs, so each warp touches whole 128-byte lines
+// of every plane.  The radial streaming shift moves values inside a pair and
+// across lanes with one shuffle per plane; the two halo columns c0 - 1 and
+// c0 + 64 are loaded by lanes 0 and 31.  The node arithmetic runs on pairs
+// with the packed FP32x2 instructions (FADD2 / FMUL2 / FFMA2) of sm_100+.
+//
+// The arithmetic is the scalar update_node() reorganised into shared
+// subexpressions and fused multiply-adds; both follow the same equations of
+// the paper and are compared against the FP64 oracle.
+
+struct F2 {
+    float2 v;
+};
+__device__ __forceinline__ F2 mk2(float a, float b)
+{
+    F2 r;
+    r.v = make_float2(a, b);
+    return r;
+}
+__device__ __forceinline__ F2 sp(float s) { return mk2(s, s); }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b)
+{
+    F2 r;
+    r.v = __fadd2_rn(a.v, b.v);
+    return r;
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b)
+{
+    F2 r;
+    r.v = __fmul2_rn(a.v, b.v);
+    return r;
+}
+// a * b + c
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c)
+{
+    F2 r;
+    r.v = __ffma2_rn(a.v, b.v, c.v);
+    return r;
+}
+// a - b, exactly (one rounding of b * (-1) + a)
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return fma2(b, sp(-1.0f), a); }
+__device__ __forceinline__ F2 rcp2(F2 a) { return mk2(__fdividef(1.0f, a.v.x), __fdividef(1.0f, a.v.y)); }
+__device__ __forceinline__ F2 sel2(bool px, bool py, F2 a, F2 b)  // per component: p ? a : b
+{
+    return mk2(px ? a.v.x : b.v.x, py ? a.v.y : b.v.y);
+}
+
+// ---- pair loads / stores ------------------------------------------------------
+
+// Counter-based random words for stochastic rounding: the PCG hash of
+// Jarzynski & Olano (2020) seeds a xorshift32 sequence (Marsaglia 2003).
+__device__ __forceinline__ uint32_t pcg_hash(uint32_t v)
+{
+    const uint32_t s = v * 747796405u + 2891336453u;
+    const uint32_t w = ((s >> ((s >> 28u) + 4u)) ^ s) * 277803737u;
+    return (w >> 22u) ^ w;
+}
+__device__ __forceinline__ uint32_t xorshift32(uint32_t x)
+{
+    x ^= x << 13;
+    x ^= x >> 17;
+    x ^= x << 5;
+    return x;
+}
+
+template <typename S> struct PairIO;
+template <> struct PairIO<float> {
+    static constexpr bool rounds = false;
+    static __device__ __forceinline__ F2 ld(const float *p)
+    {
+        F2 r;
+        r.v = *reinterpret_cast<const float2 *>(p);
+        return r;
+    }
+    static __device__ __forceinline__ void st(float *p, F2 v, uint32_t) { *reinterpret_cast<float2 *>(p) = v.v; }
+};
+// 16-bit storage: stochastic rounding (cvt.rs, sm_100+), so that the
+// rounding errors of successive steps do not accumulate a bias
+template <> struct PairIO<__half> {
+    static constexpr bool rounds = true;
+    static __device__ __forceinline__ F2 ld(const __half *p)
+    {
+        F2 r;
+        r.v = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        return r;
+    }
+    static __device__ __forceinline__ void st(__half *p, F2 v, uint32_t rbits)
+    {
+        uint32_t d;
+        // d = {hi: v.y, lo: v.x}: x stays at the lower address
+        asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v.v.y), "f"(v.v.x), "r"(rbits));
+        *reinterpret_cast<uint32_t *>(p) = d;
+    }
+};
+template <> struct PairIO<__nv_bfloat16> {
+    static constexpr bool rounds = true;
+    static __device__ __forceinline__ F2 ld(const __nv_bfloat16 *p)
+    {
+        F2 r;
+        r.v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+        return r;
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, F2 v, uint32_t rbits)
+    {
+        uint32_t d;
+        asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v.v.y), "f"(v.v.x), "r"(rbits));
+        *reinterpret_cast<uint32_t *>(p) = d;
+    }
+};
+
+// ---- the node update on pairs ------------------------------------------------
+
+struct NodeOut2 {
+    F2 f[9], g[5], h[5];
+};
+
+__device__ __forceinline__ void update_node2(const KP<float> &k, F2 iy, const F2 fv[9], const F2 gv[5],
+                                             const F2 hv[5], F2 dxuy, F2 dyux, F2 dyuy, F2 dyut, F2 dyT,
+                                             NodeOut2 &o)
+{
+    // output moments, Eq. 18, 35, 47 (deviation form)
+    const F2 a57 = fv[5] - fv[7], a86 = fv[8] - fv[6];
+    const F2 s57 = fv[5] + fv[7], s68 = fv[6] + fv[8];
+    const F2 s13 = fv[1] + fv[3], s24 = fv[2] + fv[4];
+    const F2 s5678 = s57 + s68;
+    const F2 rdo = (fv[0] + s13) + (s24 + s5678);
+    const F2 jxo = (fv[1] - fv[3]) + (a57 + a86);
+    const F2 jyo = (fv[2] - fv[4]) + (a57 - a86);
+    const F2 pso = (gv[0] + gv[1]) + (gv[2] + gv[3]) + gv[4];
+    const F2 tdo = (hv[0] + hv[1]) + (hv[2] + hv[3]) + hv[4];
+
+    // sources at the pre-collision state, two sweeps (see update_node)
+    const bool geo = !k.planar;
+    const F2 gy = geo ? iy : sp(0.0f);
+    const F2 ngy = gy * sp(-1.0f);
+    const F2 nuiy = gy * sp(k.nu);
+    const F2 Gx = (dxuy + dyux) * nuiy;
+    const F2 Gy = dyuy * (nuiy + nuiy);
+    const F2 Gw = dyut * nuiy;
+    const F2 Gt = dyT * (gy * sp(k.alpha));
+    const F2 iy2nu = nuiy * gy;
+    const F2 m2iy2nu = iy2nu * sp(-2.0f);
+    const F2 Fbx = sp(k.bfx);
+    const F2 Fb = sp(k.rho0 * k.gbeta), rho0 = sp(k.rho0), T0 = sp(k.T0), half = sp(0.5f);
+    F2 rd = rdo, jx = jxo, jy = jyo, ps = pso, td = tdo;
+    F2 MA = sp(0.0f), Fx = sp(0.0f), Fy = sp(0.0f), Sps = sp(0.0f), Sph = sp(0.0f);
+    const int sweeps = k.explicit_src ? 1 : 2;
+    for (int sw = 0; sw < sweeps; ++sw) {
+        const F2 r = rho0 + rd, ir = rcp2(r);
+        const F2 uyyn = (jy * ir) * ngy;  // -u_y / y
+        const F2 igy = ir * gy;
+        const F2 FAx = fma2(jx, uyyn, r * Gx);
+        const F2 FAy = fma2(jy, m2iy2nu, fma2(r, Gy, ((ps - jy) * (ps + jy)) * igy));
+        Sps = fma2(ps, fma2(uyyn, sp(2.0f), iy2nu * sp(-1.0f)), r * Gw);
+        Sph = fma2(uyyn, T0 + td, Gt);
+        Fx = fma2(Fb, td, FAx + Fbx);
+        Fy = FAy;
+        jx = fma2(Fx, half, jxo);
+        jy = fma2(Fy, half, jyo);
+        ps = fma2(Sps, half, pso);
+        td = fma2(Sph, half, tdo);
+        MA = (k.explicit_src ? jyo : jy) * ngy;
+        rd = fma2(MA, half, rdo);
+    }
+    const F2 r = rho0 + rd, ir = rcp2(r);
+    const F2 ux = jx * ir, uy = jy * ir;
+    const F2 phi = T0 + td;
+
+    // D2Q9 cascaded collision, Eq. 17
+    const F2 Dxx = s13 + s5678, Dyy = s24 + s5678;
+    const F2 Dxy = s57 - s68, Dxxy = a57 - a86, Dxyy = a57 + a86, Dxxyy = s5678;
+    const F2 k3 = sp(k.rho0 * (1.0f / 3.0f));
+    const F2 Kxx = k3 + Dxx, Kyy = k3 + Dyy;
+    const F2 ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const F2 uu = ux2 + uy2, ud = ux2 - uy2;
+    const F2 p3 = (fma2(rd, sp(2.0f / 3.0f), r * uu) - (Dxx + Dyy)) * sp(k.om3 * (1.0f / 12.0f));
+    const F2 c4 = sp(k.om4 * 0.25f);
+    const F2 p4 = ((r * ud) - (Dxx - Dyy)) * c4;
+    const F2 p5 = ((r * uxy) - Dxy) * c4;
+    const F2 q34p = fma2(p3, sp(3.0f), p4), q34m = fma2(p3, sp(3.0f), p4 * sp(-1.0f));
+    const F2 ch = sp(k.omhi * 0.25f);
+    const F2 m2p5 = p5 * sp(-2.0f);
+    const F2 m2Dxy = Dxy * sp(-2.0f);
+    const F2 r2 = r + r;
+    // p6: (2 r ux^2 uy + Dxxy - 2 ux Dxy - uy Kxx) omhi/4 - uy (3 p3 + p4)/2 - 2 ux p5
+    F2 Z = fma2(r2 * ux2, uy, Dxxy);
+    Z = fma2(ux, m2Dxy, Z);
+    Z = fma2(uy, Kxx * sp(-1.0f), Z);
+    const F2 p6 = fma2(Z, ch, fma2(uy, q34p * sp(-0.5f), ux * m2p5));
+    F2 Y = fma2(r2 * ux, uy2, Dxyy);
+    Y = fma2(uy, m2Dxy, Y);
+    Y = fma2(ux, Kyy * sp(-1.0f), Y);
+    const F2 p7 = fma2(Y, ch, fma2(ux, q34m * sp(-0.5f), uy * m2p5));
+    // p8
+    F2 B = fma2(ux2, Kyy, Dxxyy);
+    B = fma2(uy2, Kxx, B);
+    B = fma2(uxy, Dxy * sp(4.0f), B);
+    B = fma2(ux, Dxyy * sp(-2.0f), B);
+    B = fma2(uy, Dxxy * sp(-2.0f), B);
+    const F2 W = fma2(rd, sp(1.0f / 9.0f), (r * sp(3.0f)) * (ux2 * uy2)) - B;
+    F2 p8 = W * ch;
+    p8 = fma2(p3, sp(-2.0f), p8);
+    p8 = fma2(uy2, q34p * sp(-0.5f), p8);
+    p8 = fma2(ux2, q34m * sp(-0.5f), p8);
+    p8 = fma2(uxy, p5 * sp(-4.0f), p8);
+    p8 = fma2(uy, p6 * sp(-2.0f), p8);
+    p8 = fma2(ux, p7 * sp(-2.0f), p8);
+    // source moments, Eq. 26
+    const F2 p0 = MA * sp(1.0f / 9.0f), p1 = Fx * sp(1.0f / 6.0f), p2 = Fy * sp(1.0f / 6.0f);
+    // back-transform, Eq. 27, grouped
+    {
+        const F2 A0 = p0 - p3;
+        const F2 E = A0 + p4, Fm = A0 - p4;
+        const F2 t78m = p7 - p8, t78p = p7 + p8, t68m = p6 - p8, t68p = p6 + p8;
+        o.f[0] = fma2(p3 - p8, sp(-4.0f), fv[0] + p0);
+        o.f[1] = (fv[1] + E) + fma2(t78m, sp(2.0f), p1);
+        o.f[3] = (fv[3] + E) - fma2(t78p, sp(2.0f), p1);
+        o.f[2] = (fv[2] + Fm) + fma2(t68m, sp(2.0f), p2);
+        o.f[4] = (fv[4] + Fm) - fma2(t68p, sp(2.0f), p2);
+        const F2 B0 = fma2(p3, sp(2.0f), p0 + p8);
+        const F2 u12 = p1 + p2, v12 = p1 - p2, s67 = p6 + p7, d67 = p6 - p7;
+        const F2 C5 = B0 + p5, C6 = B0 - p5;
+        const F2 us = u12 - s67, vd = v12 + d67;
+        o.f[5] = (fv[5] + C5) + us;
+        o.f[7] = (fv[7] + C5) - us;
+        o.f[6] = (fv[6] + C6) - vd;
+        o.f[8] = (fv[8] + C6) + vd;
+    }
+
+    // D2Q5 cascaded collisions, Eq. 34 / 49 (sign reading of the paper: -)
+    const F2 coefu = fma2(sp(k.sign_lit ? 1.0f : -1.0f), uu, sp(2.0f / 3.0f));
+    const F2 coefd = sp(k.sign_lit ? 1.0f : -1.0f) * ud;
+    {
+        const F2 kxn = gv[3] - gv[1], kyn = gv[4] - gv[2];  // -kappa'_x, -kappa'_y
+        const F2 kxx = gv[1] + gv[3], kyy = gv[2] + gv[4];
+        const F2 cg = sp(k.omg * 0.5f);
+        const F2 q1 = fma2(ps, ux, kxn) * cg;
+        const F2 q2 = fma2(ps, uy, kyn) * cg;
+        const F2 m = fma2(ux, kxn, uy * kyn);  // -(ux kx + uy ky)
+        const F2 mm = fma2(ux, kxn, uy * (gv[2] - gv[4]));  // -(ux kx - uy ky)
+        const F2 X3 = fma2(ps, coefu, fma2(m, sp(-2.0f), (kxx + kyy) * sp(-1.0f)));
+        const F2 X4 = fma2(ps, coefd, fma2(mm, sp(-2.0f), (kxx - kyy) * sp(-1.0f)));
+        const F2 q3 = fma2(X3, ch, fma2(ux, q1, uy * q2));
+        const F2 q4 = fma2(X4, ch, fma2(ux, q1, uy * q2 * sp(-1.0f)));
+        const F2 q0 = Sps * sp(0.2f);
+        const F2 Q = q0 + q3, Qp = Q + q4, Qm = Q - q4;
+        o.g[0] = fma2(q3, sp(-4.0f), gv[0] + q0);
+        o.g[1] = (gv[1] + Qp) + q1;
+        o.g[3] = (gv[3] + Qp) - q1;
+        o.g[2] = (gv[2] + Qm) + q2;
+        o.g[4] = (gv[4] + Qm) - q2;
+    }
+    {
+        const F2 kxn = hv[3] - hv[1], kyn = hv[4] - hv[2];
+        const F2 Hxx = hv[1] + hv[3], Hyy = hv[2] + hv[4];
+        const F2 ct = sp(k.omh * 0.5f);
+        const F2 r1 = fma2(phi, ux, kxn) * ct;
+        const F2 r2t = fma2(phi, uy, kyn) * ct;
+        const F2 m = fma2(ux, kxn, uy * kyn);
+        const F2 mm = fma2(ux, kxn, uy * (hv[2] - hv[4]));
+        // 2 c^2 phi - (kxx + kyy) with the rest parts written out: 2/3 td - (Hxx + Hyy)
+        const F2 X3 = fma2(sp(2.0f / 3.0f), td, fma2(phi, coefu - sp(2.0f / 3.0f), fma2(m, sp(-2.0f),
+                                                                                    (Hxx + Hyy) * sp(-1.0f))));
+        const F2 X4 = fma2(phi, coefd, fma2(mm, sp(-2.0f), (Hxx - Hyy) * sp(-1.0f)));
+        const F2 r3 = fma2(X3, ch, fma2(ux, r1, uy * r2t));
+        const F2 r4 = fma2(X4, ch, fma2(ux, r1, uy * r2t * sp(-1.0f)));
+        const F2 r0 = Sph * sp(0.2f);
+        const F2 Q = r0 + r3, Qp = Q + r4, Qm = Q - r4;
+        o.h[0] = fma2(r3, sp(-4.0f), hv[0] + r0);
+        o.h[1] = (hv[1] + Qp) + r1;
+        o.h[3] = (hv[3] + Qp) - r1;
+        o.h[2] = (hv[2] + Qm) + r2t;
+        o.h[4] = (hv[4] + Qm) - r2t;
+    }
+}
+
+// ---- the march on pairs ---------------------------------------------------------
+
+struct PM2 {
+    F2 rd, ux, uy, ut, T;
+};
+
+__device__ __forceinline__ PM2 moments2(const F2 v[NQ], const KP<float> &k)
+{
+    PM2 m;
+    const F2 s13 = v[1] + v[3], s24 = v[2] + v[4], s5678 = (v[5] + v[7]) + (v[6] + v[8]);
+    m.rd = (v[0] + s13) + (s24 + s5678);
+    const F2 a57 = v[5] - v[7], a86 = v[8] - v[6];
+    const F2 jx = (v[1] - v[3]) + (a57 + a86);
+    const F2 jy = (v[2] - v[4]) + (a57 - a86);
+    const F2 ps = (v[9] + v[10]) + (v[11] + v[12]) + v[13];
+    const F2 td = (v[14] + v[15]) + (v[16] + v[17]) + v[18];
+    const F2 ir = rcp2(sp(k.rho0) + m.rd);
+    m.ux = jx * ir;
+    m.uy = jy * ir;
+    m.ut = ps * ir;
+    m.T = sp(k.T0) + td;
+    return m;
+}
+
+// values at column c - 1 (for e_y = +1) and c + 1 (for e_y = -1) of a pair;
+// lanes 0 / 31 take the halo column's value
+__device__ __forceinline__ F2 from_left(F2 v, float halo, int lane)
+{
+    float l = __shfl_up_sync(FULL, v.v.y, 1);
+    if (lane == 0) l = halo;
+    return mk2(l, v.v.x);
+}
+__device__ __forceinline__ F2 from_right(F2 v, float halo, int lane)
+{
+    float r = __shfl_down_sync(FULL, v.v.x, 1);
+    if (lane == 31) r = halo;
+    return mk2(v.v.y, r);
+}
+
+template <typename S>
+__device__ __forceinline__ void load_pair_row(const S *__restrict__ src, const KP<float> &k, int row, int Ac, int hcol,
+                                              bool hlane, F2 v[NQ], float hv[NQ])
+{
+    const S *p = src + (long long)row * k.pitch;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        v[q] = PairIO<S>::ld(p + q * k.plane + Ac);
+        hv[q] = hlane ? Cvt<S, float>::ld(p + q * k.plane + hcol) : 0.0f;
+    }
+    if (Scaled<S>::value) {
+        const float is = k.inv_scale;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            v[q] = v[q] * sp(is);
+            hv[q] *= is;
+        }
+    }
+}
+
+// Row groups of pairs, shifted in r (see groups())
+__device__ __forceinline__ void groups2(const F2 v[NQ], const float hv[NQ], int lane, F2 xm[5], F2 x0[9], F2 xp[5])
+{
+    xm[0] = v[1];
+    xm[1] = from_left(v[5], hv[5], lane);
+    xm[2] = from_right(v[8], hv[8], lane);
+    xm[3] = v[G0 + 1];
+    xm[4] = v[H0 + 1];
+    x0[0] = v[0];
+    x0[1] = from_left(v[2], hv[2], lane);
+    x0[2] = from_right(v[4], hv[4], lane);
+    x0[3] = v[G0 + 0];
+    x0[4] = from_left(v[G0 + 2], hv[G0 + 2], lane);
+    x0[5] = from_right(v[G0 + 4], hv[G0 + 4], lane);
+    x0[6] = v[H0 + 0];
+    x0[7] = from_left(v[H0 + 2], hv[H0 + 2], lane);
+    x0[8] = from_right(v[H0 + 4], hv[H0 + 4], lane);
+    xp[0] = v[3];
+    xp[1] = from_left(v[6], hv[6], lane);
+    xp[2] = from_right(v[7], hv[7], lane);
+    xp[3] = v[G0 + 3];
+    xp[4] = v[H0 + 3];
+}
+
+template <typename S>
+__device__ __forceinline__ F2 own2(const S *__restrict__ src, const KP<float> &k, int q, int row, int Ac)
+{
+    F2 v = PairIO<S>::ld(src + q * k.plane + (long long)row * k.pitch + Ac);
+    if (Scaled<S>::value) v = v * sp(k.inv_scale);
+    return v;
+}
+
+template <typename S>
+__device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__ src, S *__restrict__ dst, int c0,
+                                       int row_s, int row_e, uint32_t salt)
+{
+    const int lane = threadIdx.x & 31;
+    const int nr = k.nr, nz = k.nz;
+    const int A = c0 + 2 * lane, B = A + 1;
+    const int Amax = (nr - 1) & ~1;
+    const int Ac = A <= Amax ? A : Amax;  // even pair start inside the padded row
+    const bool outA = A < nr;
+    const bool atA0 = A == 0, atAN = A == nr - 1, atBN = B == nr - 1;
+    const bool edge_warp = __any_sync(FULL, atA0 || atAN || atBN);
+    const bool hlane = lane == 0 || lane == 31;
+    int hcol = lane == 0 ? c0 - 1 : c0 + 64;
+    hcol = hcol < 0 ? 0 : (hcol >= nr ? nr - 1 : hcol);
+    // radii and their inverses, computed in FP64 and rounded once
+    const double yAd = k.r0 + (A < nr ? A : nr - 1) + 0.5, yBd = k.r0 + (B < nr ? B : nr - 1) + 0.5;
+    const F2 y2 = mk2((float)yAd, (float)yBd);
+    const F2 iy = mk2((float)(1.0 / yAd), (float)(1.0 / yBd));
+    const float sc = k.scale;
+
+    F2 v[NQ];
+    float hv[NQ];
+    F2 xm_prev[5], xm_cur[5], x0_cur[9];
+    PM2 pm_cur;
+    float pmh_ux, pmh_uy, pmh_ut, pmh_T;  // halo column fields (lanes 0 / 31)
+    F2 uy_prev = sp(0.0f);
+    bool has_m;
+
+    auto halo_fields = [&](const float h[NQ], float &ux, float &uy, float &ut, float &T) {
+        const float rd = h[0] + h[1] + h[2] + h[3] + h[4] + h[5] + h[6] + h[7] + h[8];
+        const float ir = __fdividef(1.0f, k.rho0 + rd);
+        ux = (h[1] - h[3] + h[5] - h[6] - h[7] + h[8]) * ir;
+        uy = (h[2] - h[4] + h[5] + h[6] - h[7] - h[8]) * ir;
+        ut = (h[9] + h[10] + h[11] + h[12] + h[13]) * ir;
+        T = k.T0 + (h[14] + h[15] + h[16] + h[17] + h[18]);
+    };
+
+    if (row_s > 0 || k.xper) {
+        const int rm = row_s > 0 ? row_s - 1 : nz - 1;
+        load_pair_row<S>(src, k, rm, Ac, hcol, hlane, v, hv);
+        F2 x0t[9], xpt[5];
+        groups2(v, hv, lane, xm_prev, x0t, xpt);
+        uy_prev = moments2(v, k).uy;
+        has_m = true;
+    } else {
+        has_m = false;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) xm_prev[q] = sp(0.0f);
+    }
+    {
+        load_pair_row<S>(src, k, row_s, Ac, hcol, hlane, v, hv);
+        F2 xpt[5];
+        groups2(v, hv, lane, xm_cur, x0_cur, xpt);
+        pm_cur = moments2(v, k);
+        halo_fields(hv, pmh_ux, pmh_uy, pmh_ut, pmh_T);
+    }
+
+    for (int i = row_s; i < row_e; ++i) {
+        const bool has_p = (i + 1 < nz) || k.xper;
+        F2 xp_n[5], x0_n[9], xm_n[5];
+        PM2 pm_n;
+        float nh_ux = 0, nh_uy = 0, nh_ut = 0, nh_T = 0;
+        if (has_p) {
+            load_pair_row<S>(src, k, i + 1 < nz ? i + 1 : 0, Ac, hcol, hlane, v, hv);
+            groups2(v, hv, lane, xm_n, x0_n, xp_n);
+            pm_n = moments2(v, k);
+            halo_fields(hv, nh_ux, nh_uy, nh_ut, nh_T);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) xp_n[q] = xm_n[q] = sp(0.0f);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) x0_n[q] = sp(0.0f);
+            pm_n = pm_cur;
+        }
+
+        // pulled values of the pair
+        F2 fv[9], gv[5], hv5[5];
+        fv[1] = xm_prev[0]; fv[5] = xm_prev[1]; fv[8] = xm_prev[2]; gv[1] = xm_prev[3]; hv5[1] = xm_prev[4];
+        fv[0] = x0_cur[0]; fv[2] = x0_cur[1]; fv[4] = x0_cur[2];
+        gv[0] = x0_cur[3]; gv[2] = x0_cur[4]; gv[4] = x0_cur[5];
+        hv5[0] = x0_cur[6]; hv5[2] = x0_cur[7]; hv5[4] = x0_cur[8];
+        fv[3] = xp_n[0]; fv[6] = xp_n[1]; fv[7] = xp_n[2]; gv[3] = xp_n[3]; hv5[3] = xp_n[4];
+
+        // lateral boundaries: column 0 is always the x of a pair, column
+        // nr - 1 the x or the y
+        if (edge_warp) {
+            const float rw = k.rho0;
+            if (atA0) {
+                const int sd = 2;
+                if (k.flow[sd] == 1) {  // axis: mirror images
+                    fv[2].v.x = own2<S>(src, k, 4, i, 0).v.x;
+                    if (has_m) fv[5].v.x = own2<S>(src, k, 8, i > 0 ? i - 1 : nz - 1, 0).v.x;
+                    if (has_p) fv[6].v.x = own2<S>(src, k, 7, i + 1 < nz ? i + 1 : 0, 0).v.x;
+                } else {
+                    const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
+                    fv[2].v.x = own2<S>(src, k, 4, i, 0).v.x + rw * (6.0f / 9.0f) * uy_w;
+                    fv[5].v.x = own2<S>(src, k, 7, i, 0).v.x + rw * (6.0f / 36.0f) * (ux_w + uy_w);
+                    fv[6].v.x = own2<S>(src, k, 8, i, 0).v.x + rw * (6.0f / 36.0f) * (-ux_w + uy_w);
+                }
+                gv[2].v.x = scalar_bc<float>(k.swirl[sd], own2<S>(src, k, G0 + 4, i, 0).v.x,
+                                             wall_psi<float>(k, sd, y2.v.x), true);
+                hv5[2].v.x = scalar_bc<float>(k.heat[sd], own2<S>(src, k, H0 + 4, i, 0).v.x, k.Tw[sd] - k.T0, false);
+            }
+            if (atAN || atBN) {
+                const int sd = 3;
+                const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
+                const F2 o2 = own2<S>(src, k, 2, i, Ac), o5 = own2<S>(src, k, 5, i, Ac), o6 = own2<S>(src, k, 6, i, Ac);
+                const F2 og = own2<S>(src, k, G0 + 2, i, Ac), oh = own2<S>(src, k, H0 + 2, i, Ac);
+                const float a4 = k.rho0 * (6.0f / 9.0f) * (-uy_w);
+                const float a7 = k.rho0 * (6.0f / 36.0f) * (-ux_w - uy_w);
+                const float a8 = k.rho0 * (6.0f / 36.0f) * (ux_w - uy_w);
+                const float psw = wall_psi<float>(k, sd, 0.0f), tw = k.Tw[sd] - k.T0;
+                if (atAN) {
+                    fv[4].v.x = o2.v.x + a4;
+                    fv[7].v.x = o5.v.x + a7;
+                    fv[8].v.x = o6.v.x + a8;
+                    gv[4].v.x = scalar_bc<float>(k.swirl[sd], og.v.x, psw, true);
+                    hv5[4].v.x = scalar_bc<float>(k.heat[sd], oh.v.x, tw, false);
+                }
+                if (atBN) {
+                    fv[4].v.y = o2.v.y + a4;
+                    fv[7].v.y = o5.v.y + a7;
+                    fv[8].v.y = o6.v.y + a8;
+                    gv[4].v.y = scalar_bc<float>(k.swirl[sd], og.v.y, psw, true);
+                    hv5[4].v.y = scalar_bc<float>(k.heat[sd], oh.v.y, tw, false);
+                }
+            }
+        }
+        // end walls; they win in corners
+        if (!has_m) {
+            const int sd = 0;
+            const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
+            fv[1] = own2<S>(src, k, 3, i, Ac) + sp(k.rho0 * (6.0f / 9.0f) * ux_w);
+            fv[5] = own2<S>(src, k, 7, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (ux_w + uy_w));
+            fv[8] = own2<S>(src, k, 6, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (ux_w - uy_w));
+            const F2 og = own2<S>(src, k, G0 + 3, i, Ac), oh = own2<S>(src, k, H0 + 3, i, Ac);
+            gv[1] = mk2(scalar_bc<float>(k.swirl[sd], og.v.x, wall_psi<float>(k, sd, y2.v.x), true),
+                        scalar_bc<float>(k.swirl[sd], og.v.y, wall_psi<float>(k, sd, y2.v.y), true));
+            hv5[1] = mk2(scalar_bc<float>(k.heat[sd], oh.v.x, k.Tw[sd] - k.T0, false),
+                         scalar_bc<float>(k.heat[sd], oh.v.y, k.Tw[sd] - k.T0, false));
+        }
+        if (!has_p) {
+            const int sd = 1;
+            const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
+            fv[3] = own2<S>(src, k, 1, i, Ac) + sp(k.rho0 * (6.0f / 9.0f) * (-ux_w));
+            fv[6] = own2<S>(src, k, 8, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (-ux_w + uy_w));
+            fv[7] = own2<S>(src, k, 5, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (-ux_w - uy_w));
+            const F2 og = own2<S>(src, k, G0 + 1, i, Ac), oh = own2<S>(src, k, H0 + 1, i, Ac);
+            gv[3] = mk2(scalar_bc<float>(k.swirl[sd], og.v.x, wall_psi<float>(k, sd, y2.v.x), true),
+                        scalar_bc<float>(k.swirl[sd], og.v.y, wall_psi<float>(k, sd, y2.v.y), true));
+            hv5[3] = mk2(scalar_bc<float>(k.heat[sd], oh.v.x, k.Tw[sd] - k.T0, false),
+                         scalar_bc<float>(k.heat[sd], oh.v.y, k.Tw[sd] - k.T0, false));
+        }
+
+        // central differences of the stored-state fields, with ghosts
+        const F2 uy_xm = has_m ? uy_prev : (sp(2.0f * k.uwy[0]) - pm_cur.uy);
+        const F2 uy_xp = has_p ? pm_n.uy : (sp(2.0f * k.uwy[1]) - pm_cur.uy);
+        float lux = __shfl_up_sync(FULL, pm_cur.ux.v.y, 1), luy = __shfl_up_sync(FULL, pm_cur.uy.v.y, 1);
+        float lut = __shfl_up_sync(FULL, pm_cur.ut.v.y, 1), lT = __shfl_up_sync(FULL, pm_cur.T.v.y, 1);
+        float rux = __shfl_down_sync(FULL, pm_cur.ux.v.x, 1), ruy = __shfl_down_sync(FULL, pm_cur.uy.v.x, 1);
+        float rut = __shfl_down_sync(FULL, pm_cur.ut.v.x, 1), rT = __shfl_down_sync(FULL, pm_cur.T.v.x, 1);
+        if (lane == 0) {
+            lux = pmh_ux;
+            luy = pmh_uy;
+            lut = pmh_ut;
+            lT = pmh_T;
+        }
+        if (lane == 31) {
+            rux = pmh_ux;
+            ruy = pmh_uy;
+            rut = pmh_ut;
+            rT = pmh_T;
+        }
+        F2 Lux = mk2(lux, pm_cur.ux.v.x), Luy = mk2(luy, pm_cur.uy.v.x);
+        F2 Lut = mk2(lut, pm_cur.ut.v.x), LT = mk2(lT, pm_cur.T.v.x);
+        F2 Rux = mk2(pm_cur.ux.v.y, rux), Ruy = mk2(pm_cur.uy.v.y, ruy);
+        F2 Rut = mk2(pm_cur.ut.v.y, rut), RT = mk2(pm_cur.T.v.y, rT);
+        if (edge_warp) {
+            if (atA0) {
+                const int sd = 2;
+                const float ux = pm_cur.ux.v.x, uy = pm_cur.uy.v.x, ut = pm_cur.ut.v.x, T = pm_cur.T.v.x;
+                if (k.flow[sd] == 1) {
+                    Lux.v.x = ux;
+                    Luy.v.x = -uy;
+                } else {
+                    Lux.v.x = 2.0f * k.uwx[sd] - ux;
+                    Luy.v.x = 2.0f * k.uwy[sd] - uy;
+                }
+                const int sw = k.swirl[sd], ht = k.heat[sd];
+                Lut.v.x = sw == 2 ? -ut : (sw == 0 ? 2.0f * k.omega[sd] * (float)k.r0 - ut : ut);
+                LT.v.x = ht == 0 ? 2.0f * k.Tw[sd] - T : T;
+            }
+            if (atAN || atBN) {
+                const int sd = 3;
+                const int sw = k.swirl[sd], ht = k.heat[sd];
+                const float Ro = (float)(k.r0 + k.nr);
+                if (atAN) {
+                    const float ux = pm_cur.ux.v.x, uy = pm_cur.uy.v.x, ut = pm_cur.ut.v.x, T = pm_cur.T.v.x;
+                    Rux.v.x = 2.0f * k.uwx[sd] - ux;
+                    Ruy.v.x = 2.0f * k.uwy[sd] - uy;
+                    Rut.v.x = sw == 0 ? 2.0f * k.omega[sd] * Ro - ut : ut;
+                    RT.v.x = ht == 0 ? 2.0f * k.Tw[sd] - T : T;
+                }
+                if (atBN) {
+                    const float ux = pm_cur.ux.v.y, uy = pm_cur.uy.v.y, ut = pm_cur.ut.v.y, T = pm_cur.T.v.y;
+                    Rux.v.y = 2.0f * k.uwx[sd] - ux;
+                    Ruy.v.y = 2.0f * k.uwy[sd] - uy;
+                    Rut.v.y = sw == 0 ? 2.0f * k.omega[sd] * Ro - ut : ut;
+                    RT.v.y = ht == 0 ? 2.0f * k.Tw[sd] - T : T;
+                }
+            }
+        }
+        const F2 hf = sp(0.5f);
+        const F2 dxuy = (uy_xp - uy_xm) * hf;
+        const F2 dyux = (Rux - Lux) * hf;
+        const F2 dyuy = (Ruy - Luy) * hf;
+        const F2 dyut = (Rut - Lut) * hf;
+        const F2 dyT = (RT - LT) * hf;
+
+        NodeOut2 o;
+        update_node2(k, iy, fv, gv, hv5, dxuy, dyux, dyuy, dyut, dyT, o);
+
+        if (outA) {
+            S *p = dst + (long long)i * k.pitch + A;
+            uint32_t w = 0;
+            if (PairIO<S>::rounds) w = pcg_hash((uint32_t)(i * k.pitch + A) ^ salt) | 1u;
+            const F2 m = sp(Scaled<S>::value ? sc : 1.0f);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                if (PairIO<S>::rounds) w = xorshift32(w);
+                PairIO<S>::st(p + q * k.plane, Scaled<S>::value ? o.f[q] * m : o.f[q], w);
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                if (PairIO<S>::rounds) w = xorshift32(w);
+                PairIO<S>::st(p + (G0 + q) * k.plane, Scaled<S>::value ? o.g[q] * m : o.g[q], w);
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                if (PairIO<S>::rounds) w = xorshift32(w);
+                PairIO<S>::st(p + (H0 + q) * k.plane, Scaled<S>::value ? o.h[q] * m : o.h[q], w);
+            }
+        }
+
+        // rotate the row window
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            xm_prev[q] = xm_cur[q];
+            xm_cur[q] = xm_n[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) x0_cur[q] = x0_n[q];
+        uy_prev = pm_cur.uy;
+        pm_cur = pm_n;
+        pmh_ux = nh_ux;
+        pmh_uy = nh_uy;
+        pmh_ut = nh_ut;
+        pmh_T = nh_T;
+        has_m = true;
+    }
+}
