@@ -165,7 +165,8 @@ LB_EXPORT lb_status lb_step(lb_ctx *ctx, int32_t nsteps);
 LB_EXPORT lb_status lb_get_fields(lb_ctx *ctx, double *host_fields);
 
 /* Diagnostics of the current state.  Synchronous; status LB_ERR_DIVERGED
- * when a field is not finite or rho leaves [0.5, 1.5]. */
+ * when a field is not finite or rho leaves [0.5, 1.5], LB_ERR_TIMEOUT when a
+ * bounded wait of a step kernel ran out (the state is then not valid). */
 LB_EXPORT lb_status lb_diagnostics(lb_ctx *ctx, lb_diag *out);
 
 /* Distributions as absolute values, host [19][nz][nr] doubles: f0..f8,
@@ -181,9 +182,11 @@ LB_EXPORT lb_status lb_set_state(lb_ctx *ctx, const void *host, size_t bytes);
 /* Steps taken since the last reset. */
 LB_EXPORT lb_status lb_get_step(const lb_ctx *ctx, int64_t *step);
 
-/* Tune the launch: rows per z-segment of a warp (0 = automatic) and warps
- * per block (0 = automatic).  Results do not depend on the launch shape. */
-LB_EXPORT lb_status lb_set_launch(lb_ctx *ctx, int32_t seg_rows, int32_t warps_per_block);
+/* Tune the launch: rows per z-segment of a warp (0 = automatic), warps per
+ * block (0 = automatic, at most 8) and how the FP32 / 16-bit step fetches
+ * its rows (0 = automatic, 1 = plain loads, 2 = TMA bulk tensor copies into
+ * shared memory).  Results do not depend on the launch shape. */
+LB_EXPORT lb_status lb_set_launch(lb_ctx *ctx, int32_t seg_rows, int32_t warps_per_block, int32_t row_fetch);
 
 /* Diagnostics of a state held in the caller's device memory, with no context
  * and no scratch memory from the caller; the paper has no counterpart.
@@ -210,6 +213,27 @@ LB_EXPORT lb_status lb_set_launch(lb_ctx *ctx, int32_t seg_rows, int32_t warps_p
 LB_EXPORT lb_status lb_diagnostics_static(const lb_grid_desc *desc, const lb_params *params,
                                           const void *dev_state, int64_t step, void *cuda_stream,
                                           lb_diag *out);
+
+/* ---- batches: many lattices advanced together --------------------------------
+ * A batch advances a set of FP32 or 16-bit lattices (any shapes, any
+ * parameters) with one persistent kernel launch per step over all their
+ * 64-column x z-segment tiles, replayed from a CUDA graph of graph_steps
+ * launches when the stream is not the legacy default stream.  Each lattice's
+ * update is the one lb_step performs (same arithmetic, same rounding bits).
+ * While a batch exists its lattices are stepped through it only; their step
+ * counters and current buffers follow the batch, so lb_diagnostics and the
+ * other per-lattice calls keep working.  The caller owns the device buffer
+ * (lb_batch_required_bytes, 256-byte aligned) holding the descriptors. */
+typedef struct lb_batch lb_batch;
+LB_EXPORT lb_status lb_batch_required_bytes(int32_t n, size_t *bytes);
+LB_EXPORT lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_buf, size_t bytes, void *cuda_stream,
+                                    lb_batch **out);
+/* rows per z-segment (0 = keep), warps per block (0 = keep), launches per
+ * CUDA graph (0 or 1 = no graph) */
+LB_EXPORT lb_status lb_batch_set_launch(lb_batch *b, int32_t seg_rows, int32_t warps_per_block,
+                                        int32_t graph_steps);
+LB_EXPORT lb_status lb_batch_step(lb_batch *b, int32_t nsteps);
+LB_EXPORT lb_status lb_batch_destroy(lb_batch *b);
 
 /* Release the context (not the caller's buffer or stream). */
 LB_EXPORT lb_status lb_destroy(lb_ctx *ctx);

@@ -1,0 +1,55 @@
+"""Many lattices advanced together through the C ABI batch calls.
+
+All lattices of a batch share the storage type (FP32 or 16-bit); their
+shapes and parameters may differ.  One persistent kernel launch per step
+covers every tile of every lattice, replayed from a CUDA graph.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _abi
+from .solver import Solver
+
+
+class Batch:
+    def __init__(self, solvers: list[Solver], stream: torch.cuda.Stream | None = None,
+                 seg_rows: int = 0, warps_per_block: int = 0, graph_steps: int = 8):
+        if not solvers:
+            raise ValueError("empty batch")
+        self.L = _abi.load()
+        self.solvers = list(solvers)
+        self.stream = stream or solvers[0].stream
+        n = len(self.solvers)
+        nb = C.c_size_t()
+        _abi.check(self.L.lb_batch_required_bytes(n, C.byref(nb)))
+        self.buffer = torch.empty(int(nb.value), dtype=torch.uint8, device=self.solvers[0].device)
+        arr = (C.c_void_p * n)(*[s.ctx.value for s in self.solvers])
+        h = C.c_void_p()
+        _abi.check(self.L.lb_batch_create(arr, n, C.c_void_p(self.buffer.data_ptr()), self.buffer.numel(),
+                                          C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self.h = h
+        self.set_launch(seg_rows, warps_per_block, graph_steps)
+
+    def set_launch(self, seg_rows: int = 0, warps_per_block: int = 0, graph_steps: int = 8) -> None:
+        _abi.check(self.L.lb_batch_set_launch(self.h, int(seg_rows), int(warps_per_block), int(graph_steps)))
+
+    def step(self, n: int = 1) -> None:
+        _abi.check(self.L.lb_batch_step(self.h, int(n)))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.L.lb_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nodes(self) -> int:
+        return sum(s.n for s in self.solvers)

@@ -13,6 +13,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/lb.h"
 #include "lb_internal.h"
@@ -34,6 +35,9 @@ struct lb_ctx {
     int64_t step;
     Launch launch;
     bool launch_auto;
+    alignas(64) unsigned char tmap[2][128];  // TMA tensor maps of dist[0], dist[1]
+    bool tmap_ready;
+    int *status;  // device status word (bounded-wait timeouts of the step kernel)
     char err[256];
 };
 
@@ -194,6 +198,8 @@ lb_status lb_create(const lb_grid_desc *desc, void *dev_buf, size_t bytes, void 
     c->dist[1] = c->buf + dist;
     c->partial = (double *)(c->buf + 2 * dist);
     c->result = (double *)(c->buf + 2 * dist + align256((size_t)lbk::MAX_DIAG_BLOCKS * lbk::NSUM * sizeof(double)));
+    c->status = (int *)((char *)c->result + 128);
+    c->tmap_ready = false;
     c->stream = (cudaStream_t)cuda_stream;
     c->cur = 0;
     c->step = 0;
@@ -231,8 +237,9 @@ lb_status lb_set_params(lb_ctx *ctx, const lb_params *p)
         h.omega[s] = p->side[s].omega;
         h.Tw[s] = p->side[s].T_w;
     }
-    // rest state: every stored deviation is zero
+    // rest state: every stored deviation is zero; clear the status word
     cudaError_t e = cudaMemsetAsync(ctx->dist[0], 0, ctx->dist_bytes, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reset");
     ctx->cur = 0;
     ctx->step = 0;
@@ -272,9 +279,17 @@ lb_status lb_step(lb_ctx *ctx, int32_t nsteps)
     lb_status st = need_params(ctx);
     if (st != LB_OK) return st;
     if (nsteps < 0) return fail(ctx, LB_ERR_ARG, "nsteps < 0");
+    if (ctx->hp.storage != LB_FP64 && !ctx->tmap_ready) {
+        for (int b = 0; b < 2; ++b) {
+            cudaError_t e = lbk::make_tensor_map(ctx->hp, ctx->dist[b], ctx->tmap[b]);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor map");
+        }
+        ctx->tmap_ready = true;
+    }
     for (int32_t t = 0; t < nsteps; ++t) {
+        const void *map = ctx->tmap_ready ? ctx->tmap[ctx->cur] : nullptr;
         cudaError_t e = lbk::launch_step(ctx->hp, ctx->launch, ctx->dist[ctx->cur], ctx->dist[1 - ctx->cur],
-                                         (unsigned long long)ctx->step, ctx->stream);
+                                         (unsigned long long)ctx->step, map, ctx->status, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
         ctx->cur ^= 1;
         ctx->step += 1;
@@ -315,10 +330,12 @@ lb_status lb_diagnostics(lb_ctx *ctx, lb_diag *out)
     if (!out) return fail(ctx, LB_ERR_ARG, "out is NULL");
     const HostParams &h = ctx->hp;
     double res[lbk::NSUM];
+    int kstatus = 0;
     cudaError_t e = lbk::launch_diag(h, diag_launch(ctx), ctx->dist[ctx->cur], ctx->partial,
                                      (double *)ctx->dist[1 - ctx->cur], ctx->result, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "diagnostics kernel");
-    e = cudaMemcpyAsync(res, ctx->result, sizeof(res), cudaMemcpyDeviceToHost, ctx->stream);
+    e = cudaMemcpyAsync(&kstatus, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(res, ctx->result, sizeof(res), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "diagnostics download");
     std::memset(out, 0, sizeof(*out));
@@ -348,7 +365,7 @@ lb_status lb_diagnostics(lb_ctx *ctx, lb_diag *out)
     out->nu_avg = (a >= 0 && b >= 0) ? 0.5 * (out->nu_i + out->nu_o) : out->nu_i;
     out->step = ctx->step;
     const bool bad = res[8] > 0.0 || !std::isfinite(res[0]) || !std::isfinite(res[2]);
-    out->status = bad ? LB_ERR_DIVERGED : LB_OK;
+    out->status = kstatus ? kstatus : (bad ? LB_ERR_DIVERGED : LB_OK);
     return LB_OK;
 }
 
@@ -448,15 +465,18 @@ lb_status lb_get_step(const lb_ctx *ctx, int64_t *step)
     return LB_OK;
 }
 
-lb_status lb_set_launch(lb_ctx *ctx, int32_t seg_rows, int32_t warps_per_block)
+lb_status lb_set_launch(lb_ctx *ctx, int32_t seg_rows, int32_t warps_per_block, int32_t row_fetch)
 {
     if (!ctx) return fail(nullptr, LB_ERR_ARG, "ctx is NULL");
-    if (seg_rows < 0 || warps_per_block < 0 || warps_per_block > 8)
-        return fail(ctx, LB_ERR_ARG, "seg_rows >= 0, 0 <= warps_per_block <= 8");
+    if (seg_rows < 0 || warps_per_block < 0 || warps_per_block > 8 || row_fetch < 0 || row_fetch > 2)
+        return fail(ctx, LB_ERR_ARG, "seg_rows >= 0, 0 <= warps_per_block <= 8, 0 <= row_fetch <= 2");
+    if (seg_rows && (ctx->hp.nz + seg_rows - 1) / seg_rows > 65535)
+        return fail(ctx, LB_ERR_ARG, "seg_rows too small for nz (more than 65535 segments)");
     Launch d = lbk::default_launch(ctx->hp);
     ctx->launch.seg_rows = seg_rows ? seg_rows : d.seg_rows;
     ctx->launch.warps_per_block = warps_per_block ? warps_per_block : d.warps_per_block;
-    ctx->launch_auto = seg_rows == 0 && warps_per_block == 0;
+    ctx->launch.use_tma = row_fetch == 0 ? d.use_tma : (row_fetch == 2 && ctx->hp.storage != LB_FP64 ? 1 : 0);
+    ctx->launch_auto = seg_rows == 0 && warps_per_block == 0 && row_fetch == 0;
     return LB_OK;
 }
 
@@ -467,5 +487,180 @@ lb_status lb_destroy(lb_ctx *ctx)
 }
 
 const char *lb_last_error(const lb_ctx *ctx) { return ctx ? ctx->err : g_err; }
+
+// ---- batches ---------------------------------------------------------------------
+
+struct lb_batch {
+    std::vector<lb_ctx *> ctxs;
+    std::vector<unsigned long long> step0;
+    std::vector<int> parity0;
+    int storage;
+    char *buf;
+    size_t bytes;
+    void *d_desc;
+    int *d_prefix;
+    void *d_ctl;
+    cudaStream_t stream;
+    int seg_rows, wpb, blocks, total, graph_steps;
+    unsigned long long counter;
+    cudaGraphExec_t gexec;
+    bool graph_valid;
+    std::vector<unsigned char> hdesc;
+    std::vector<int> hprefix;
+};
+
+static size_t batch_layout(int32_t n, size_t *desc_off, size_t *prefix_off, size_t *ctl_off)
+{
+    const size_t d = align256((size_t)n * lbk::batch_desc_bytes());
+    const size_t p = align256((size_t)(n + 1) * sizeof(int));
+    *desc_off = 0;
+    *prefix_off = d;
+    *ctl_off = d + p;
+    return d + p + align256(lbk::batch_ctl_bytes());
+}
+
+static lb_status batch_upload(lb_batch *b)
+{
+    const int n = (int)b->ctxs.size();
+    const size_t db = lbk::batch_desc_bytes();
+    b->hdesc.assign((size_t)n * db, 0);
+    b->hprefix.assign((size_t)n + 1, 0);
+    for (int m = 0; m < n; ++m) {
+        lb_ctx *c = b->ctxs[m];
+        lbk::batch_fill_desc(c->hp, c->dist[0], c->dist[1], b->step0[m], b->parity0[m], b->seg_rows,
+                             b->hdesc.data() + (size_t)m * db);
+        b->hprefix[m + 1] = b->hprefix[m] + lbk::batch_items(c->hp, b->seg_rows);
+    }
+    b->total = b->hprefix[n];
+    cudaError_t e = cudaMemcpyAsync(b->d_desc, b->hdesc.data(), b->hdesc.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_prefix, b->hprefix.data(), b->hprefix.size() * sizeof(int), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch upload");
+    if (b->graph_valid) {
+        cudaGraphExecDestroy(b->gexec);
+        b->graph_valid = false;
+    }
+    return LB_OK;
+}
+
+lb_status lb_batch_required_bytes(int32_t n, size_t *bytes)
+{
+    if (n < 1 || !bytes) return fail(nullptr, LB_ERR_ARG, "n >= 1 and bytes required");
+    size_t a, b, c;
+    *bytes = batch_layout(n, &a, &b, &c);
+    return LB_OK;
+}
+
+lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_buf, size_t bytes, void *cuda_stream,
+                          lb_batch **out)
+{
+    if (!out || !ctxs || n < 1 || !dev_buf) return fail(nullptr, LB_ERR_ARG, "NULL argument or n < 1");
+    *out = nullptr;
+    size_t doff, poff, coff;
+    const size_t need = batch_layout(n, &doff, &poff, &coff);
+    if (bytes < need) return fail(nullptr, LB_ERR_NOMEM, "batch buffer holds %zu bytes, %zu needed", bytes, need);
+    if (((uintptr_t)dev_buf & 255) != 0) return fail(nullptr, LB_ERR_ARG, "dev_buf must be 256-byte aligned");
+    const int storage = ctxs[0] ? ctxs[0]->hp.storage : -1;
+    if (storage == LB_FP64 || storage < 0) return fail(nullptr, LB_ERR_ARG, "batches take FP32 or 16-bit lattices");
+    for (int m = 0; m < n; ++m) {
+        if (!ctxs[m] || !ctxs[m]->params_set) return fail(nullptr, LB_ERR_STATE, "lattice %d has no parameters", m);
+        if (ctxs[m]->hp.storage != storage) return fail(nullptr, LB_ERR_ARG, "lattices of a batch share the storage");
+        for (int q = 0; q < m; ++q)
+            if (ctxs[q] == ctxs[m]) return fail(nullptr, LB_ERR_ARG, "lattice %d appears twice", m);
+    }
+    lb_batch *b = new (std::nothrow) lb_batch();
+    if (!b) return fail(nullptr, LB_ERR_NOMEM, "host allocation failed");
+    b->ctxs.assign(ctxs, ctxs + n);
+    for (int m = 0; m < n; ++m) {
+        b->step0.push_back((unsigned long long)ctxs[m]->step);
+        b->parity0.push_back(ctxs[m]->cur);
+    }
+    b->storage = storage;
+    b->buf = (char *)dev_buf;
+    b->bytes = bytes;
+    b->d_desc = b->buf + doff;
+    b->d_prefix = (int *)(b->buf + poff);
+    b->d_ctl = b->buf + coff;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->seg_rows = 8;
+    b->wpb = 2;
+    b->graph_steps = 8;
+    b->counter = 0;
+    b->graph_valid = false;
+    b->blocks = lbk::batch_grid(storage, b->wpb);
+    cudaError_t e = cudaMemsetAsync(b->d_ctl, 0, lbk::batch_ctl_bytes(), b->stream);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(nullptr, e, "batch reset");
+    }
+    lb_status st = batch_upload(b);
+    if (st != LB_OK) {
+        delete b;
+        return st;
+    }
+    *out = b;
+    return LB_OK;
+}
+
+lb_status lb_batch_set_launch(lb_batch *b, int32_t seg_rows, int32_t warps_per_block, int32_t graph_steps)
+{
+    if (!b || seg_rows < 0 || warps_per_block < 0 || warps_per_block > 8 || graph_steps < 0)
+        return fail(nullptr, LB_ERR_ARG, "seg_rows >= 0, 0 <= warps_per_block <= 8, graph_steps >= 0");
+    if (seg_rows) b->seg_rows = seg_rows;
+    if (warps_per_block) {
+        b->wpb = warps_per_block;
+        b->blocks = lbk::batch_grid(b->storage, b->wpb);
+    }
+    b->graph_steps = graph_steps;
+    return batch_upload(b);
+}
+
+lb_status lb_batch_step(lb_batch *b, int32_t nsteps)
+{
+    if (!b || nsteps < 0) return fail(nullptr, LB_ERR_ARG, "batch is NULL or nsteps < 0");
+    int32_t left = nsteps;
+    const bool use_graph = b->graph_steps > 1 && b->stream != nullptr && left >= b->graph_steps;
+    if (use_graph && !b->graph_valid) {
+        cudaGraph_t g;
+        cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        for (int t = 0; e == cudaSuccess && t < b->graph_steps; ++t)
+            e = lbk::launch_batch(b->storage, b->d_desc, b->d_prefix, (int)b->ctxs.size(), b->total, b->d_ctl,
+                                  b->wpb, b->blocks, b->stream);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&b->gexec, g, 0);
+            cudaGraphDestroy(g);
+        }
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch graph");
+        b->graph_valid = true;
+    }
+    if (use_graph)
+        for (; left >= b->graph_steps; left -= b->graph_steps) {
+            cudaError_t e = cudaGraphLaunch(b->gexec, b->stream);
+            if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch graph launch");
+        }
+    for (; left > 0; --left) {
+        cudaError_t e = lbk::launch_batch(b->storage, b->d_desc, b->d_prefix, (int)b->ctxs.size(), b->total,
+                                          b->d_ctl, b->wpb, b->blocks, b->stream);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch launch");
+    }
+    b->counter += (unsigned long long)nsteps;
+    for (size_t m = 0; m < b->ctxs.size(); ++m) {
+        lb_ctx *c = b->ctxs[m];
+        c->step = (int64_t)(b->step0[m] + b->counter);
+        c->cur = (int)((b->parity0[m] + b->counter) & 1ULL);
+    }
+    return LB_OK;
+}
+
+lb_status lb_batch_destroy(lb_batch *b)
+{
+    if (b && b->graph_valid) cudaGraphExecDestroy(b->gexec);
+    delete b;
+    return LB_OK;
+}
 
 }  // extern "C"

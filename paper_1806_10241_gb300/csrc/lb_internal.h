@@ -31,12 +31,16 @@ struct HostParams {
 struct Launch {
     int seg_rows;             // rows per z-segment
     int warps_per_block;
+    int use_tma;              // TMA row fetches (FP32 / 16-bit storage)
 };
 
 // One time step src -> dst; `step` seeds the stochastic rounding of 16-bit
 // storage.
 cudaError_t launch_step(const HostParams &p, const Launch &l, const void *src, void *dst,
-                        unsigned long long step, cudaStream_t s);
+                        unsigned long long step, const void *tmap, int *status, cudaStream_t s);
+// Tensor map (CUtensorMap, 128 bytes) of a distribution buffer for the TMA
+// row fetches of the FP32 / 16-bit step.
+cudaError_t make_tensor_map(const HostParams &p, void *buf, void *map_out);
 // Pre-collision fields of rows [row0, row1) into out[5][row1-row0][nr] (double).
 cudaError_t launch_fields(const HostParams &p, const Launch &l, const void *src, double *out,
                           int row0, int row1, cudaStream_t s);
@@ -56,6 +60,16 @@ cudaError_t launch_import(const HostParams &p, const double *in, void *dst, int 
                           cudaStream_t s);
 
 size_t storage_bytes(int storage);
+
+// Batched step (FP32 / 16-bit storage): device descriptors built on the host
+size_t batch_desc_bytes();
+size_t batch_ctl_bytes();
+int batch_items(const HostParams &h, int seg_rows);
+void batch_fill_desc(const HostParams &h, void *buf0, void *buf1, unsigned long long step0, int parity0,
+                     int seg_rows, void *out);
+int batch_grid(int storage, int wpb);
+cudaError_t launch_batch(int storage, const void *desc, const int *prefix, int n, int total, void *ctl, int wpb,
+                         int blocks, cudaStream_t s);
 // Message for lb_last_error(NULL) on this thread.
 void set_global_error(const char *msg);
 Launch default_launch(const HostParams &p);

@@ -25,6 +25,8 @@
 #include <mutex>
 #include <type_traits>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -678,7 +680,7 @@ __global__ void __maxnreg__(255) k_step64(KP<C> k, const S *__restrict__ src, S 
 
 // FP32-compute step on column pairs (lb_pair.cuh): 64 aligned columns per warp
 #ifndef LB_STEP2_MAXREG
-#define LB_STEP2_MAXREG 168
+#define LB_STEP2_MAXREG 232
 #endif
 template <typename S>
 __global__ void __maxnreg__(LB_STEP2_MAXREG) k_step2(KP<float> k, const S *__restrict__ src, S *__restrict__ dst,
@@ -686,9 +688,52 @@ __global__ void __maxnreg__(LB_STEP2_MAXREG) k_step2(KP<float> k, const S *__res
 {
     const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (warp >= nwin2) return;
+    const int lane = threadIdx.x & 31;
     const int s = blockIdx.y * seg_rows;
     const int e = min(k.nz, s + seg_rows);
-    march2<S>(k, src, dst, warp * 64, s, e, salt);
+    const int A = warp * 64 + 2 * lane;
+    const int Amax = (k.nr - 1) & ~1;
+    int hcol = lane == 0 ? warp * 64 - 1 : warp * 64 + 64;
+    hcol = hcol < 0 ? 0 : (hcol >= k.nr ? k.nr - 1 : hcol);
+    RowDirect<S> rs{src, &k, A <= Amax ? A : Amax, hcol, (s > 0 || k.xper) ? s - 1 : s, k.nz, 0,
+                    lane == 0 || lane == 31};
+    march2<S>(k, src, dst, warp * 64, s, e, salt, rs);
+}
+
+// The same step with the rows of each warp fetched by TMA into a ring of
+// shared-memory stages (one bulk tensor copy per row), so that a warp has
+// up to kTmaStages rows in flight without holding them in registers.
+template <typename S>
+__global__ void __maxnreg__(LB_STEP2_MAXREG)
+    k_step2_tma(KP<float> k, const __grid_constant__ CUtensorMap map, const S *__restrict__ src,
+                S *__restrict__ dst, int seg_rows, int nwin2, uint32_t salt, int *status)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int wib = threadIdx.x >> 5;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (warp >= nwin2) return;
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.y * seg_rows;
+    const int e = min(k.nz, s + seg_rows);
+    const bool has_m = s > 0 || k.xper, has_last = e < k.nz || k.xper;
+    const int nrows = (e - s) + (has_m ? 1 : 0) + (has_last ? 1 : 0);
+    const int per_warp = kTmaStages * TmaGeom<S>::stage_bytes + 128;  // keeps every ring 128-byte aligned
+    unsigned char *ring = smem + per_warp * wib;
+    RowTma<S> rs;
+    rs.map = &map;
+    rs.k = &k;
+    rs.ring = ring;
+    rs.ring_s = smem_u32(ring);
+    rs.bar_s = smem_u32(ring + kTmaStages * TmaGeom<S>::stage_bytes);
+    rs.first = has_m ? s - 1 : s;
+    rs.nrows = nrows;
+    rs.nz = k.nz;
+    rs.taken = 0;
+    rs.lane = lane;
+    rs.x0 = warp * 64 - TmaGeom<S>::off;
+    rs.status = status;
+    rs.start();
+    march2<S>(k, src, dst, warp * 64, s, e, salt, rs);
 }
 
 template <typename S, typename C>
@@ -943,21 +988,101 @@ __global__ void k_import(HostParams h, const double *__restrict__ in, S *__restr
 
 int nwindows(int nr) { return (nr + OUT_COLS - 1) / OUT_COLS; }
 
-int nwindows2(int nr) { return (nr + 63) / 64; }
+// ---- batched step: many lattices, one launch per step ----------------------------
 
-uint32_t step_salt(unsigned long long step)
+// SplitMix64 finaliser of a step counter (the same function as step_salt on
+// the host: a lattice draws the same rounding bits alone and in a batch)
+__host__ __device__ __forceinline__ uint32_t salt_of(unsigned long long step)
 {
-    // SplitMix64 finaliser of the step counter (random bits of the stochastic
-    // rounding differ from step to step)
     unsigned long long z = step + 0x9E3779B97F4A7C15ULL;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
     return (uint32_t)(z ^ (z >> 31));
 }
 
+struct BatchDesc {
+    KP<float> k;
+    void *buf[2];
+    unsigned long long step0;  // the lattice's step count when the batch was made
+    int parity0;               // its current buffer then
+    int nwin2, seg_rows, pad;
+};
+
+struct BatchCtl {
+    unsigned long long counter;  // steps the batch has taken
+    unsigned int ticket;         // blocks finished in the running launch
+    unsigned int pad;
+};
+
+// Work items (instance, 64-column window, z-segment) are numbered by a prefix
+// sum over the instances and dealt to the warps of a persistent grid.  The
+// last block to finish advances the step counter, so every launch is the same
+// and a CUDA graph of several launches can be replayed.
+template <typename S>
+__global__ void __maxnreg__(LB_STEP2_MAXREG) k_batch(const BatchDesc *__restrict__ d, const int *__restrict__ prefix,
+                                                     int n, int total, BatchCtl *ctl)
+{
+    __shared__ KP<float> skp[8];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const unsigned long long t = *(volatile unsigned long long *)&ctl->counter;
+    for (int item = blockIdx.x * wpb + wib; item < total; item += gridDim.x * wpb) {
+        int lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (prefix[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const BatchDesc *bd = d + lo;
+        __syncwarp();
+        {
+            const uint32_t *s = reinterpret_cast<const uint32_t *>(&bd->k);
+            uint32_t *o = reinterpret_cast<uint32_t *>(&skp[wib]);
+            for (int w = lane; w < (int)(sizeof(KP<float>) / 4); w += 32) o[w] = s[w];
+        }
+        __syncwarp();
+        const KP<float> &k = skp[wib];
+        const int local = item - prefix[lo];
+        const int nw2 = bd->nwin2;
+        const int w = local % nw2, sg = local / nw2;
+        const int cur = (bd->parity0 + (int)(t & 1ULL)) & 1;
+        const S *src = (const S *)bd->buf[cur];
+        S *dst = (S *)bd->buf[cur ^ 1];
+        const int seg = bd->seg_rows;
+        const int s = sg * seg, e = min(k.nz, s + seg);
+        const int A = w * 64 + 2 * lane, Amax = (k.nr - 1) & ~1;
+        int hcol = lane == 0 ? w * 64 - 1 : w * 64 + 64;
+        hcol = hcol < 0 ? 0 : (hcol >= k.nr ? k.nr - 1 : hcol);
+        RowDirect<S> rs{src, &k, A <= Amax ? A : Amax, hcol, (s > 0 || k.xper) ? s - 1 : s, k.nz, 0,
+                        lane == 0 || lane == 31};
+        march2<S>(k, src, dst, w * 64, s, e, salt_of(bd->step0 + t), rs);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int tk = atomicAdd(&ctl->ticket, 1u);
+        if (tk == gridDim.x - 1) {
+            ctl->ticket = 0;
+            ctl->counter = t + 1;
+            __threadfence();
+        }
+    }
+}
+
+int nwindows2(int nr) { return (nr + 63) / 64; }
+
+// random bits of the stochastic rounding differ from step to step
+uint32_t step_salt(unsigned long long step) { return salt_of(step); }
+
+template <typename S>
+size_t tma_smem_bytes(int wpb)
+{
+    return (size_t)wpb * (kTmaStages * TmaGeom<S>::stage_bytes + 128);
+}
+
 template <typename S, typename C>
 cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *dst, unsigned long long step,
-                   cudaStream_t s)
+                   const void *tmap, int *status, cudaStream_t s)
 {
     const KP<C> k = make_kp<C>(h);
     const int wpb = l.warps_per_block;
@@ -969,7 +1094,20 @@ cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *
     } else {
         const int nwin2 = nwindows2(h.nr);
         dim3 grid((nwin2 + wpb - 1) / wpb, (h.nz + seg - 1) / seg);
-        k_step2<S><<<grid, 32 * wpb, 0, s>>>(k, (const S *)src, (S *)dst, seg, nwin2, step_salt(step));
+        if (tmap && l.use_tma) {
+            const size_t sm = tma_smem_bytes<S>(wpb);
+            static bool attr_set = false;
+            if (!attr_set) {
+                cudaError_t e = cudaFuncSetAttribute(k_step2_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)tma_smem_bytes<S>(8));
+                if (e != cudaSuccess) return e;
+                attr_set = true;
+            }
+            k_step2_tma<S><<<grid, 32 * wpb, sm, s>>>(k, *(const CUtensorMap *)tmap, (const S *)src, (S *)dst, seg,
+                                                       nwin2, step_salt(step), status);
+        } else {
+            k_step2<S><<<grid, 32 * wpb, 0, s>>>(k, (const S *)src, (S *)dst, seg, nwin2, step_salt(step));
+        }
     }
     return cudaGetLastError();
 }
@@ -1019,7 +1157,8 @@ size_t storage_bytes(int storage)
 Launch default_launch(const HostParams &p)
 {
     Launch l;
-    l.warps_per_block = 4;
+    l.warps_per_block = p.storage == ST_FP64 ? 4 : 2;
+    l.use_tma = p.storage != ST_FP64 ? 1 : 0;
     // 32-row segments (two halo rows per segment, 6 %), fewer when the
     // lattice would otherwise leave SMs idle
     const int nwin = p.storage == ST_FP64 ? nwindows(p.nr) : nwindows2(p.nr);
@@ -1044,9 +1183,36 @@ Launch default_launch(const HostParams &p)
     }
 
 cudaError_t launch_step(const HostParams &p, const Launch &l, const void *src, void *dst, unsigned long long step,
-                        cudaStream_t s)
+                        const void *tmap, int *status, cudaStream_t s)
 {
-    DISPATCH(p, (step_t<S, C>(p, l, src, dst, step, s)));
+    DISPATCH(p, (step_t<S, C>(p, l, src, dst, step, tmap, status, s)));
+}
+
+// Tensor map of one distribution buffer for the TMA row fetches: a 3-D view
+// [19 planes][nz rows][pitch columns], box of TmaGeom::cols x 1 x 19.
+cudaError_t make_tensor_map(const HostParams &p, void *buf, void *map_out)
+{
+    if (p.storage == ST_FP64) return cudaErrorInvalidValue;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const int es = (int)storage_bytes(p.storage);
+    const CUtensorMapDataType dt = p.storage == ST_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : p.storage == ST_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)p.pitch, (cuuint64_t)p.nz, (cuuint64_t)NQ};
+    const cuuint64_t strides[2] = {(cuuint64_t)p.pitch * es, (cuuint64_t)p.plane * es};
+    const cuuint32_t box[3] = {(cuuint32_t)(64 + 2 * (16 / es)), 1u, (cuuint32_t)NQ};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = encode((CUtensorMap *)map_out, dt, 3, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fields(const HostParams &p, const Launch &l, const void *src, double *out, int row0, int row1,
@@ -1089,6 +1255,69 @@ cudaError_t launch_import(const HostParams &p, const double *in, void *dst, int 
 {
     const int nb = blocks_for((long long)(row1 - row0) * p.nr);
     DISPATCH_S(p, (k_import<S><<<nb, 256, 0, s>>>(p, in, (S *)dst, row0, row1)));
+    return cudaGetLastError();
+}
+
+}  // namespace lbk
+
+namespace lbk {
+
+size_t batch_desc_bytes() { return sizeof(BatchDesc); }
+size_t batch_ctl_bytes() { return sizeof(BatchCtl); }
+
+int batch_items(const HostParams &h, int seg_rows)
+{
+    return nwindows2(h.nr) * ((h.nz + seg_rows - 1) / seg_rows);
+}
+
+void batch_fill_desc(const HostParams &h, void *buf0, void *buf1, unsigned long long step0, int parity0,
+                     int seg_rows, void *out)
+{
+    BatchDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.k = make_kp<float>(h);
+    d.buf[0] = buf0;
+    d.buf[1] = buf1;
+    d.step0 = step0;
+    d.parity0 = parity0;
+    d.nwin2 = nwindows2(h.nr);
+    d.seg_rows = seg_rows;
+    std::memcpy(out, &d, sizeof(d));
+}
+
+int batch_grid(int storage, int wpb)
+{
+    int dev = 0, sms = 152, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    switch (storage) {
+        case ST_FP32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<float>, 32 * wpb, 0); break;
+        case ST_FP16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<__half>, 32 * wpb, 0); break;
+        case ST_BF16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<__nv_bfloat16>, 32 * wpb, 0); break;
+        default: per = 1;
+    }
+    return sms * (per > 0 ? per : 1);
+}
+
+cudaError_t launch_batch(int storage, const void *desc, const int *prefix, int n, int total, void *ctl, int wpb,
+                         int blocks, cudaStream_t s)
+{
+    const int need = (total + wpb - 1) / wpb;
+    const int grid = blocks < need ? blocks : need;
+    if (grid < 1) return cudaSuccess;
+    switch (storage) {
+        case ST_FP32:
+            k_batch<float><<<grid, 32 * wpb, 0, s>>>((const BatchDesc *)desc, prefix, n, total, (BatchCtl *)ctl);
+            break;
+        case ST_FP16:
+            k_batch<__half><<<grid, 32 * wpb, 0, s>>>((const BatchDesc *)desc, prefix, n, total, (BatchCtl *)ctl);
+            break;
+        case ST_BF16:
+            k_batch<__nv_bfloat16>
+                <<<grid, 32 * wpb, 0, s>>>((const BatchDesc *)desc, prefix, n, total, (BatchCtl *)ctl);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -370,9 +370,135 @@ __device__ __forceinline__ F2 own2(const S *__restrict__ src, const KP<float> &k
     return v;
 }
 
-template <typename S>
+// ---- row sources ------------------------------------------------------------------
+//
+// march2 consumes the rows of its segment strictly in order (row s-1 when it
+// exists, s, s+1, ..., and the look-ahead row e when it exists, indices taken
+// modulo nz).  A row source delivers them as pairs plus the lane's halo value.
+
+// Plain global loads.
+template <typename S> struct RowDirect {
+    const S *src;
+    const KP<float> *k;
+    int Ac, hcol, first, nz, taken;
+    bool hlane;
+    __device__ __forceinline__ bool get(F2 v[NQ], float hv[NQ])
+    {
+        int row = first + taken++;
+        row = row >= nz ? row - nz : (row < 0 ? row + nz : row);
+        load_pair_row<S>(src, *k, row, Ac, hcol, hlane, v, hv);
+        return true;
+    }
+    __device__ __forceinline__ void finish() {}
+};
+
+// TMA ring (sm_90+ bulk tensor copies): one 3-D box per row -- kTmaCols
+// columns starting kTmaOff columns left of the warp's window, one row, all 19
+// planes -- into a stage of shared memory, completion signalled on an
+// mbarrier.  Lane 0 issues the copies; every wait is bounded and a timeout
+// sets the device status word instead of spinning for ever.
+template <typename S> struct TmaGeom {
+    static constexpr int es = (int)sizeof(S);
+    static constexpr int off = 16 / es;               // x start stays 16-byte aligned
+    static constexpr int cols = 64 + 2 * off;          // 72 (FP32) or 80 (16-bit) columns
+    static constexpr int box_bytes = NQ * cols * es;
+    static constexpr int stage_bytes = (box_bytes + 127) / 128 * 128;
+};
+constexpr int kTmaStages = 3;
+constexpr int kTmaWaitLimit = 1 << 22;  // bounded mbarrier polls (about a second)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+template <typename S> struct RowTma {
+    const CUtensorMap *map;
+    const KP<float> *k;
+    const unsigned char *ring;  // this warp's stages
+    uint32_t ring_s, bar_s;     // shared addresses of the stages and of the barriers
+    int first, nrows, nz, taken, lane, x0;
+    int *status;
+
+    __device__ __forceinline__ void issue(int f)
+    {
+        int row = first + f;
+        row = row >= nz ? row - nz : (row < 0 ? row + nz : row);
+        const int st = f % kTmaStages;
+        const uint32_t bar = bar_s + 8u * st, dst = ring_s + (uint32_t)(TmaGeom<S>::stage_bytes * st);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((uint32_t)TmaGeom<S>::box_bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];" ::"r"(dst),
+            "l"((unsigned long long)map), "r"(x0), "r"(row), "r"(0), "r"(bar)
+            : "memory");
+    }
+
+    __device__ __forceinline__ void start()
+    {
+        if (lane == 0) {
+            for (int s = 0; s < kTmaStages; ++s)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s + 8u * s) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            for (int f = 0; f < kTmaStages && f < nrows; ++f) issue(f);
+        }
+        __syncwarp();
+    }
+
+    __device__ __forceinline__ bool wait_stage(int t)
+    {
+        const int st = t % kTmaStages;
+        const uint32_t parity = (uint32_t)((t / kTmaStages) & 1);
+        uint32_t ok = 0;
+        for (int it = 0; it < kTmaWaitLimit && !ok; ++it)
+            asm volatile(
+                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                : "=r"(ok)
+                : "r"(bar_s + 8u * st), "r"(parity)
+                : "memory");
+        return ok != 0;
+    }
+
+    __device__ __forceinline__ bool get(F2 v[NQ], float hv[NQ])
+    {
+        const int t = taken++;
+        if (!__all_sync(FULL, wait_stage(t))) {
+            if (lane == 0) atomicExch(status, (int)LB_ERR_TIMEOUT);
+            return false;
+        }
+        const S *b = reinterpret_cast<const S *>(ring + TmaGeom<S>::stage_bytes * (t % kTmaStages));
+        constexpr int C = TmaGeom<S>::cols, O = TmaGeom<S>::off;
+        const int hc = lane == 0 ? O - 1 : O + 64;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            v[q] = PairIO<S>::ld(b + q * C + O + 2 * lane);
+            hv[q] = Cvt<S, float>::ld(b + q * C + hc);
+        }
+        if (Scaled<S>::value) {
+            const float is = k->inv_scale;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                v[q] = v[q] * sp(is);
+                hv[q] *= is;
+            }
+        }
+        __syncwarp();  // every lane has read the stage
+        if (lane == 0 && t + kTmaStages < nrows) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(t + kTmaStages);
+        }
+        return true;
+    }
+
+    // after an error: give the copies still in flight a bounded wait
+    __device__ __forceinline__ void finish()
+    {
+        for (int t = taken; t < nrows && t < taken + kTmaStages; ++t) (void)wait_stage(t);
+    }
+};
+
+template <typename S, typename RS>
 __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__ src, S *__restrict__ dst, int c0,
-                                       int row_s, int row_e, uint32_t salt)
+                                       int row_s, int row_e, uint32_t salt, RS &rs)
 {
     const int lane = threadIdx.x & 31;
     const int nr = k.nr, nz = k.nz;
@@ -382,7 +508,6 @@ __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__
     const bool outA = A < nr;
     const bool atA0 = A == 0, atAN = A == nr - 1, atBN = B == nr - 1;
     const bool edge_warp = __any_sync(FULL, atA0 || atAN || atBN);
-    const bool hlane = lane == 0 || lane == 31;
     int hcol = lane == 0 ? c0 - 1 : c0 + 64;
     hcol = hcol < 0 ? 0 : (hcol >= nr ? nr - 1 : hcol);
     // radii and their inverses, computed in FP64 and rounded once
@@ -409,8 +534,7 @@ __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__
     };
 
     if (row_s > 0 || k.xper) {
-        const int rm = row_s > 0 ? row_s - 1 : nz - 1;
-        load_pair_row<S>(src, k, rm, Ac, hcol, hlane, v, hv);
+        if (!rs.get(v, hv)) return rs.finish();
         F2 x0t[9], xpt[5];
         groups2(v, hv, lane, xm_prev, x0t, xpt);
         uy_prev = moments2(v, k).uy;
@@ -421,7 +545,7 @@ __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__
         for (int q = 0; q < 5; ++q) xm_prev[q] = sp(0.0f);
     }
     {
-        load_pair_row<S>(src, k, row_s, Ac, hcol, hlane, v, hv);
+        if (!rs.get(v, hv)) return rs.finish();
         F2 xpt[5];
         groups2(v, hv, lane, xm_cur, x0_cur, xpt);
         pm_cur = moments2(v, k);
@@ -434,7 +558,7 @@ __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__
         PM2 pm_n;
         float nh_ux = 0, nh_uy = 0, nh_ut = 0, nh_T = 0;
         if (has_p) {
-            load_pair_row<S>(src, k, i + 1 < nz ? i + 1 : 0, Ac, hcol, hlane, v, hv);
+            if (!rs.get(v, hv)) return rs.finish();
             groups2(v, hv, lane, xm_n, x0_n, xp_n);
             pm_n = moments2(v, k);
             halo_fields(hv, nh_ux, nh_uy, nh_ut, nh_T);

@@ -79,8 +79,9 @@ class Solver:
         return self.nr * self.nz
 
     # -- the ABI --------------------------------------------------------------
-    def set_launch(self, seg_rows: int = 0, warps_per_block: int = 0) -> None:
-        self._check(self.L.lb_set_launch(self.ctx, int(seg_rows), int(warps_per_block)))
+    def set_launch(self, seg_rows: int = 0, warps_per_block: int = 0, row_fetch: int = 0) -> None:
+        """row_fetch: 0 automatic, 1 plain loads, 2 TMA (FP32 / 16-bit storage)."""
+        self._check(self.L.lb_set_launch(self.ctx, int(seg_rows), int(warps_per_block), int(row_fetch)))
 
     def init_fields(self, fields: np.ndarray) -> None:
         a = np.ascontiguousarray(fields, np.float64).reshape(5, self.nz, self.nr)

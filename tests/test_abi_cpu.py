@@ -106,7 +106,8 @@ def test_create_and_parameter_validation_without_device_work(lib):
         bad["sides"][0]["flow"] = W.FLOW_PERIODIC  # only one end periodic
         assert lib.lb_set_params(ctx, C.byref(_abi.make_params(bad))) == _abi.LB_ERR_ARG
         assert b"periodic" in lib.lb_last_error(ctx)
-        assert lib.lb_set_launch(ctx, 16, 9) == _abi.LB_ERR_ARG
+        assert lib.lb_set_launch(ctx, 16, 9, 0) == _abi.LB_ERR_ARG
+        assert lib.lb_set_launch(ctx, 16, 4, 3) == _abi.LB_ERR_ARG
         s = C.c_int64()
         assert lib.lb_get_step(ctx, C.byref(s)) == _abi.LB_OK and s.value == 0
     finally:

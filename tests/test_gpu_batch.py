@@ -1,0 +1,80 @@
+"""Batched step: each lattice's result is the same alone and in a batch of
+uneven lattices (bitwise: the per-lattice arithmetic and rounding bits are
+identical), and matches the FP64 oracle like a single lattice does."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_10241_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_10241_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _cases():
+    cs = W.batched_instances(count=6, lo=20, hi=150)
+    cs.append(W.swirling_cylinder(nr=70, nz=45, Re=200.0, Ra=1e4, amp=1e-3, seed=9))
+    cs.append(W.taylor_couette(R_o=40, beta=0.5))
+    return cs
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_batch_equals_individual_runs(storage):
+    from paper_1806_10241_gb300.batch import Batch
+    from paper_1806_10241_gb300.solver import Solver
+    stream = torch.cuda.Stream()
+    cases = _cases()
+    alone = []
+    for c in cases:
+        s = Solver(c.params, storage=storage, stream=stream)
+        s.init_fields(c.fields)
+        s.step(37)
+        alone.append(s.get_dist())
+    mixed = []
+    for c in cases:
+        s = Solver(c.params, storage=storage, stream=stream)
+        s.init_fields(c.fields)
+        mixed.append(s)
+    b = Batch(mixed, stream=stream, graph_steps=8)
+    b.step(5)
+    b.set_launch(seg_rows=5, warps_per_block=4, graph_steps=4)
+    b.step(32)  # 8 graph replays of 4 launches
+    torch.cuda.synchronize()
+    for c, a, s in zip(cases, alone, mixed):
+        assert s.step_count == 37
+        assert np.array_equal(s.get_dist(), a), c.name
+    b.close()
+
+
+def test_batch_matches_oracle_fp32():
+    from paper_1806_10241_gb300.batch import Batch
+    from paper_1806_10241_gb300.solver import Solver
+    cases = _cases()[:4]
+    sols = []
+    for c in cases:
+        s = Solver(c.params, storage="fp32")
+        s.init_fields(c.fields)
+        sols.append(s)
+    b = Batch(sols, stream=torch.cuda.Stream(), graph_steps=10)
+    b.step(300)
+    torch.cuda.synchronize()
+    for c, s in zip(cases, sols):
+        o = oracle.Oracle(c.params)
+        o.init_fields(c.fields)
+        o.step(300)
+        got, want = s.fields(), o.fields()
+        for q in (1, 2, 4):
+            n = np.linalg.norm(want[q])
+            if n > 0:
+                assert np.linalg.norm(got[q] - want[q]) / n < 1e-5, (c.name, q)
+        d = s.diag()
+        assert d["status"] == 0 and d["step"] == 300
