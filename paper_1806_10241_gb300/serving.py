@@ -1,0 +1,220 @@
+"""Continuous-batching server of axisymmetric solve requests.
+
+Requests (workloads.Request: arrival time + lattice) arrive as a stream.  The
+server keeps every admitted lattice resident on the device and advances all
+of them together with the batched step (one persistent launch per step,
+replayed from a CUDA graph).  Between rounds it
+  * admits the requests that have arrived while their bytes fit the device
+    memory budget (lb_required_bytes against free HBM less a reserve),
+  * evaluates the diagnostics of each active lattice every `check_every`
+    steps and retires the ones that reached the steady state
+    (|Nu(t) - Nu(t - window)| < tol), hit the step cap or diverged,
+  * rebuilds the batch when its membership changed.
+Latency of a request = finish time - arrival time.  `run_sequential` serves
+the same stream one plain solve at a time, for comparison.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from .batch import Batch
+from .solver import Solver, required_bytes
+from .workloads import Request
+
+
+@dataclass
+class Record:
+    rid: int
+    name: str
+    nodes: int
+    arrival: float
+    admitted: float = -1.0
+    finished: float = -1.0
+    steps: int = 0
+    nu: float = float("nan")
+    status: str = "pending"  # converged | capped | diverged
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+@dataclass
+class Report:
+    records: list
+    makespan: float
+    mode: str
+    extra: dict = field(default_factory=dict)
+
+    def summary(self) -> dict:
+        done = [r for r in self.records if r.finished >= 0]
+        lat = np.array([r.latency for r in done]) if done else np.array([np.nan])
+        ok = [r for r in done if r.status == "converged"]
+        steps_nodes = sum(r.steps * r.nodes for r in done)
+        return {"mode": self.mode, "requests": len(self.records), "completed": len(done),
+                "converged": len(ok), "capped": sum(r.status == "capped" for r in done),
+                "diverged": sum(r.status == "diverged" for r in done),
+                "makespan_s": round(self.makespan, 3),
+                "solves_per_s": round(len(done) / self.makespan, 3) if self.makespan > 0 else None,
+                "p50_latency_s": round(float(np.percentile(lat, 50)), 3),
+                "p99_latency_s": round(float(np.percentile(lat, 99)), 3),
+                "MLUPS": round(steps_nodes / self.makespan / 1e6, 1) if self.makespan > 0 else None,
+                **self.extra}
+
+
+class _Active:
+    def __init__(self, req: Request, solver: Solver, rec: Record, nbytes: int):
+        self.req, self.solver, self.rec, self.nbytes = req, solver, rec, nbytes
+        self.history: list[tuple[int, float]] = []  # (step, Nu)
+
+
+def _steady(history: list[tuple[int, float]], window: int, tol: float) -> bool:
+    if len(history) < 2:
+        return False
+    s_now, nu_now = history[-1]
+    for s, nu in reversed(history[:-1]):
+        if s_now - s >= window:
+            return abs(nu_now - nu) < tol
+    return False
+
+
+class Server:
+    def __init__(self, storage: str = "fp16", steps_per_round: int = 500, check_every: int = 500,
+                 window: int = 1000, tol: float = 1e-6, max_steps: int = 200_000,
+                 hbm_budget: int | None = None, reserve_bytes: int = 1 << 30, max_active: int = 512,
+                 graph_steps: int = 10, seg_rows: int = 0, warps_per_block: int = 0,
+                 device: str = "cuda", keep_results: bool = False):
+        if check_every % steps_per_round:
+            raise ValueError("check_every must be a multiple of steps_per_round")
+        self.storage = storage
+        self.steps_per_round = steps_per_round
+        self.check_every = check_every
+        self.window = window
+        self.tol = tol
+        self.max_steps = max_steps
+        self.max_active = max_active
+        self.graph_steps = graph_steps
+        self.seg_rows = seg_rows
+        self.warps_per_block = warps_per_block
+        self.device = torch.device(device)
+        self.keep_results = keep_results
+        self.results: dict[int, np.ndarray] = {}  # final distributions (keep_results)
+        self.max_concurrent = 0
+        free, _ = torch.cuda.mem_get_info(self.device)
+        self.budget = (free - reserve_bytes) if hbm_budget is None else int(hbm_budget)
+        self.stream = torch.cuda.Stream(self.device)
+
+    # -- one request's admission and retirement ---------------------------------------
+    def _admit(self, req: Request, now: float, rec: Record) -> _Active:
+        s = Solver(req.case.params, storage=self.storage, device=self.device, stream=self.stream)
+        s.init_fields(req.case.fields)
+        rec.admitted = now
+        return _Active(req, s, rec, required_bytes(req.case.params, self.storage))
+
+    def _check(self, a: _Active) -> bool:
+        """Diagnostics of an active lattice; True when it is finished."""
+        d = a.solver.diag()
+        a.rec.steps = d["step"]
+        a.rec.nu = d["nu_avg"]
+        a.history.append((d["step"], d["nu_avg"]))
+        if d["status"] != 0 or not np.isfinite(d["nu_avg"]):
+            a.rec.status = "diverged"
+            return True
+        if _steady(a.history, self.window, self.tol):
+            a.rec.status = "converged"
+            return True
+        if d["step"] >= self.max_steps:
+            a.rec.status = "capped"
+            return True
+        return False
+
+    def run(self, requests: list[Request], clock=time.perf_counter) -> Report:
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        records = {r.rid: Record(r.rid, r.case.name, r.case.nr * r.case.nz, r.arrival) for r in requests}
+        active: list[_Active] = []
+        used = 0
+        batch = None
+        dirty = True
+        t0 = clock()
+        rounds = 0
+        while pending or active:
+            now = clock() - t0
+            # admit what has arrived, in arrival order, while it fits
+            while pending and pending[0].arrival <= now and len(active) < self.max_active:
+                need = required_bytes(pending[0].case.params, self.storage)
+                if used + need > self.budget:
+                    if not active:  # can never fit: reject
+                        req = pending.popleft()
+                        rec = records[req.rid]
+                        rec.status, rec.finished = "rejected", clock() - t0
+                    break
+                req = pending.popleft()
+                active.append(self._admit(req, now, records[req.rid]))
+                used += active[-1].nbytes
+                self.max_concurrent = max(self.max_concurrent, len(active))
+                dirty = True
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, min(0.05, pending[0].arrival - (clock() - t0))))
+                continue
+            if dirty:
+                if batch is not None:
+                    batch.close()
+                batch = Batch([a.solver for a in active], stream=self.stream, seg_rows=self.seg_rows,
+                              warps_per_block=self.warps_per_block, graph_steps=self.graph_steps)
+                dirty = False
+            batch.step(self.steps_per_round)
+            rounds += 1
+            # every lattice of the batch has taken the same number of rounds
+            # since its admission; check those at a multiple of check_every
+            finished = []
+            for a in active:
+                if a.solver.step_count % self.check_every == 0 and self._check(a):
+                    finished.append(a)
+            if finished:
+                now = clock() - t0
+                for a in finished:
+                    a.rec.finished = now
+                    if self.keep_results:
+                        self.results[a.rec.rid] = a.solver.get_dist()
+                    used -= a.nbytes
+                    active.remove(a)
+                    a.solver.close()
+                batch.close()
+                batch = None
+                dirty = True
+        if batch is not None:
+            batch.close()
+        torch.cuda.synchronize(self.device)
+        return Report(list(records.values()), clock() - t0, "batched",
+                      {"rounds": rounds, "storage": self.storage, "max_concurrent": self.max_concurrent})
+
+    def run_sequential(self, requests: list[Request], storage: str = "fp32",
+                       clock=time.perf_counter) -> Report:
+        """The same stream served one plain solve at a time (no batching)."""
+        queue = deque(sorted(requests, key=lambda r: r.arrival))
+        records = {r.rid: Record(r.rid, r.case.name, r.case.nr * r.case.nz, r.arrival) for r in requests}
+        t0 = clock()
+        while queue:
+            req = queue.popleft()
+            now = clock() - t0
+            if req.arrival > now:
+                time.sleep(req.arrival - now)
+            rec = records[req.rid]
+            s = Solver(req.case.params, storage=storage, device=self.device, stream=self.stream)
+            s.init_fields(req.case.fields)
+            a = _Active(req, s, rec, 0)
+            rec.admitted = clock() - t0
+            while True:
+                s.step(self.steps_per_round)
+                if s.step_count % self.check_every == 0 and self._check(a):
+                    break
+            rec.finished = clock() - t0
+            s.close()
+        torch.cuda.synchronize(self.device)
+        return Report(list(records.values()), clock() - t0, "sequential", {"storage": storage})

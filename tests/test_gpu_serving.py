@@ -1,0 +1,79 @@
+"""Serving loop: continuous batching with admission by a device-memory
+budget.  Every request finishes, requests overlap on the device, and each
+result is bitwise the one of the same request run alone for the same steps."""
+import numpy as np
+import pytest
+
+from paper_1806_10241_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_10241_gb300 import build
+    build.build()
+
+
+def _stream(n=7):
+    out = []
+    for i in range(n):
+        nr = 16 + 6 * i
+        c = W.annulus_convection(nr=nr, nz=nr + 8 * (i % 3), Ra=10 ** (3 + (i % 3) * 0.5), amp=1e-4, seed=i,
+                                 swirl_inner=0.01 * (i % 2))
+        c.name = f"r{i}"
+        out.append(W.Request(i, 0.02 * i, c))
+    return out
+
+
+def _alone(req, steps, storage, rounds):
+    from paper_1806_10241_gb300.solver import Solver
+    s = Solver(req.case.params, storage=storage)
+    s.init_fields(req.case.fields)
+    for _ in range(steps // rounds):
+        s.step(rounds)
+    return s.get_dist()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_server_results_equal_solo_runs(storage):
+    from paper_1806_10241_gb300.serving import Server
+    reqs = _stream()
+    srv = Server(storage=storage, steps_per_round=100, check_every=200, window=400, tol=1e-7,
+                 max_steps=2000, keep_results=True, graph_steps=5)
+    rep = srv.run(reqs)
+    summ = rep.summary()
+    assert summ["completed"] == len(reqs)
+    assert srv.max_concurrent >= 2  # requests overlapped on the device
+    for r in rep.records:
+        assert r.status in ("converged", "capped"), (r.name, r.status)
+        assert r.steps > 0 and r.latency > 0
+        want = _alone(reqs[r.rid], r.steps, storage, 100)
+        assert np.array_equal(srv.results[r.rid], want), r.name
+
+
+def test_admission_respects_the_memory_budget():
+    from paper_1806_10241_gb300.serving import Server
+    from paper_1806_10241_gb300.solver import required_bytes
+    reqs = [W.Request(r.rid, 0.0, r.case) for r in _stream(6)]  # a burst: all at once
+    biggest = max(required_bytes(r.case.params, "fp16") for r in reqs)
+    srv = Server(storage="fp16", steps_per_round=100, check_every=200, window=400, tol=1e-7, max_steps=800,
+                 hbm_budget=2 * biggest + 1)
+    rep = srv.run(reqs)
+    assert rep.summary()["completed"] == len(reqs)
+    assert srv.max_concurrent <= 2
+    # later requests waited for memory
+    waited = [r for r in rep.records if r.admitted - r.arrival > 1e-3]
+    assert waited
+
+
+def test_sequential_baseline_runs():
+    from paper_1806_10241_gb300.serving import Server
+    reqs = _stream(3)
+    srv = Server(storage="fp16", steps_per_round=100, check_every=200, window=400, tol=1e-7, max_steps=600)
+    rep = srv.run_sequential(reqs, storage="fp32")
+    s = rep.summary()
+    assert s["completed"] == 3 and s["p99_latency_s"] >= s["p50_latency_s"]
