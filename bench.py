@@ -183,28 +183,36 @@ def run_serving(args):
     """--workload serving: a Poisson stream of solve requests served by the
     continuous-batching server (16-bit storage) and, for comparison, by
     sequential plain FP32 solves.  Reduced from the full stream (2000
-    requests, nr up to 1024, 200k-step cap) so that both finish in minutes:
-    the sizes, counts and cap are in the line's config."""
+    requests, nr up to 1024) to 40 requests with nr in 64..128 so that both
+    finish in minutes; the steady-state test and the 200k-step cap are the
+    full stream's.  The sizes, counts and cap are in the line's config."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_1806_10241_gb300 import workloads as W
     from paper_1806_10241_gb300.serving import Server
     torch.cuda.set_device(0)
-    reqs = W.serving_requests(count=args.requests, rate=50.0, seed=0, nr_lo=32, nr_hi=args.nr_hi)
+    reqs = W.serving_requests(count=args.requests, rate=50.0, seed=0, nr_lo=args.nr_lo, nr_hi=args.nr_hi)
     kw = dict(steps_per_round=500, check_every=500, window=1000, tol=1e-6, max_steps=args.max_steps)
     srv = Server(storage=args.serve_storage, graph_steps=10, **kw)
-    rb = srv.run(reqs).summary()
-    seq = Server(storage=args.serve_storage, **kw).run_sequential(reqs, storage="fp32").summary()
+    rep_b = srv.run(reqs)
+    rep_s = Server(storage=args.serve_storage, **kw).run_sequential(reqs, storage="fp32")
+    rb, seq = rep_b.summary(), rep_s.summary()
+    # the served Nu of each request against its sequential FP32 solve
+    nu_s = {r.rid: r.nu for r in rep_s.records}
+    dnu = [abs(r.nu - nu_s[r.rid]) / abs(nu_s[r.rid]) for r in rep_b.records
+           if r.finished >= 0 and nu_s.get(r.rid) not in (None, 0.0)]
     line = {"metric": METRIC, "value": rb["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.serve_storage], "data": "synthetic",
             "config": {"workload": "Poisson stream of axisymmetric solve requests (60 % annulus convection, "
                                    "40 % swirling cylinder), continuous batching",
-                       "requests": args.requests, "rate_per_s": 50.0, "nr": f"U{{32..{args.nr_hi}}}",
+                       "requests": args.requests, "rate_per_s": 50.0, "nr": f"U{{{args.nr_lo}..{args.nr_hi}}}",
                        "nz": "nr * U{1,2}", "Ra": "log-U[1e3,1e5]", "steady": "|dNu| < 1e-6 over 1000 steps",
                        "max_steps": args.max_steps},
             "p50_latency_s": rb["p50_latency_s"], "p99_latency_s": rb["p99_latency_s"],
+            "nu_rel_diff_vs_sequential_fp32": {"max": float(max(dnu)) if dnu else None,
+                                               "median": float(sorted(dnu)[len(dnu) // 2]) if dnu else None},
             "batched": rb, "sequential_fp32": seq,
             "speedup_solves_per_s": round(rb["solves_per_s"] / seq["solves_per_s"], 2)
             if seq["solves_per_s"] else None}
@@ -269,8 +277,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="cylinder", choices=["cylinder", "serving"])
     ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--nr-lo", dest="nr_lo", type=int, default=64)
     ap.add_argument("--nr-hi", dest="nr_hi", type=int, default=128)
-    ap.add_argument("--max-steps", dest="max_steps", type=int, default=20000)
+    ap.add_argument("--max-steps", dest="max_steps", type=int, default=200_000)
     ap.add_argument("--serve-storage", dest="serve_storage", default="fp16", choices=["fp16", "bf16", "fp32"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()

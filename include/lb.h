@@ -140,7 +140,9 @@ typedef struct {
 } lb_diag;
 
 /* Bytes of device memory a lattice of this shape needs (2 distribution
- * buffers + reduction scratch).  Returns LB_ERR_ARG for an invalid desc. */
+ * buffers + reduction scratch + a table of the column radii y and 1/y,
+ * Eq. 2 with half-way walls, computed in FP64 and rounded once).  Returns
+ * LB_ERR_ARG for an invalid desc. */
 LB_EXPORT lb_status lb_required_bytes(const lb_grid_desc *desc, size_t *bytes);
 
 /* Create a context on the caller's device buffer (>= lb_required_bytes,
@@ -150,7 +152,7 @@ LB_EXPORT lb_status lb_create(const lb_grid_desc *desc, void *dev_buf, size_t by
                     lb_ctx **out);
 
 /* Set the parameters and reset the state to rest: rho0, u = 0, u_theta = 0,
- * T = T0, step = 0. */
+ * T = T0, step = 0; writes the radius table.  Synchronises the stream. */
 LB_EXPORT lb_status lb_set_params(lb_ctx *ctx, const lb_params *params);
 
 /* Initialise every node to the equilibria of host fields [5][nz][nr]:

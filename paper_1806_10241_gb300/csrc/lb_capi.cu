@@ -1,7 +1,9 @@
 // Host side of the C ABI declared in include/lb.h.
 //
 // Device memory layout inside the caller's buffer (256-byte aligned parts):
-//   [A: 19 planes][B: 19 planes][partial sums][result]
+//   [A: 19 planes][B: 19 planes][partial sums][result, status][radius table]
+// The radius table holds y = r_inner + j + 1/2 and 1/y per column (pitch
+// entries each), computed in FP64 and rounded once to FP32.
 // A and B alternate as source and destination of the time steps; the one
 // that is not current doubles as staging space for host exchanges and for
 // the temperature field of the diagnostics.
@@ -86,6 +88,8 @@ lb_status check_desc(const lb_grid_desc *d, size_t *plane, size_t *dist_bytes)
 
 size_t scratch_bytes() { return align256((size_t)lbk::MAX_DIAG_BLOCKS * lbk::NSUM * sizeof(double)) + 256; }
 
+size_t table_bytes(int pitch) { return align256(2 * (size_t)pitch * sizeof(float)); }
+
 lb_status validate_params(lb_ctx *ctx, const lb_params *p)
 {
     const HostParams &h = ctx->hp;
@@ -165,7 +169,7 @@ lb_status lb_required_bytes(const lb_grid_desc *desc, size_t *bytes)
     lb_status st = check_desc(desc, &plane, &dist);
     if (st != LB_OK) return st;
     if (!bytes) return fail(nullptr, LB_ERR_ARG, "bytes is NULL");
-    *bytes = 2 * dist + scratch_bytes();
+    *bytes = 2 * dist + scratch_bytes() + table_bytes(pitch_for(desc->nr, desc->storage));
     return LB_OK;
 }
 
@@ -176,7 +180,7 @@ lb_status lb_create(const lb_grid_desc *desc, void *dev_buf, size_t bytes, void 
     size_t plane, dist;
     lb_status st = check_desc(desc, &plane, &dist);
     if (st != LB_OK) return st;
-    const size_t need = 2 * dist + scratch_bytes();
+    const size_t need = 2 * dist + scratch_bytes() + table_bytes(pitch_for(desc->nr, desc->storage));
     if (!dev_buf) return fail(nullptr, LB_ERR_ARG, "dev_buf is NULL");
     if (((uintptr_t)dev_buf & 255) != 0) return fail(nullptr, LB_ERR_ARG, "dev_buf must be 256-byte aligned");
     if (bytes < need) return fail(nullptr, LB_ERR_NOMEM, "buffer holds %zu bytes, %zu needed", bytes, need);
@@ -199,6 +203,7 @@ lb_status lb_create(const lb_grid_desc *desc, void *dev_buf, size_t bytes, void 
     c->partial = (double *)(c->buf + 2 * dist);
     c->result = (double *)(c->buf + 2 * dist + align256((size_t)lbk::MAX_DIAG_BLOCKS * lbk::NSUM * sizeof(double)));
     c->status = (int *)((char *)c->result + 128);
+    h.ytab = (const float *)(c->buf + 2 * dist + scratch_bytes());
     c->tmap_ready = false;
     c->stream = (cudaStream_t)cuda_stream;
     c->cur = 0;
@@ -237,9 +242,20 @@ lb_status lb_set_params(lb_ctx *ctx, const lb_params *p)
         h.omega[s] = p->side[s].omega;
         h.Tw[s] = p->side[s].T_w;
     }
-    // rest state: every stored deviation is zero; clear the status word
+    // rest state: every stored deviation is zero; clear the status word;
+    // radius table (entries past nr - 1 repeat the last radius)
+    std::vector<float> tab(2 * (size_t)h.pitch);
+    for (int j = 0; j < h.pitch; ++j) {
+        const double y = h.r0 + (j < h.nr ? j : h.nr - 1) + 0.5;
+        tab[j] = (float)y;
+        tab[h.pitch + j] = (float)(1.0 / y);
+    }
     cudaError_t e = cudaMemsetAsync(ctx->dist[0], 0, ctx->dist_bytes, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((void *)h.ytab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice,
+                            ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // tab is freed on return
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reset");
     ctx->cur = 0;
     ctx->step = 0;

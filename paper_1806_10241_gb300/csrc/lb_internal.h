@@ -26,6 +26,7 @@ struct HostParams {
     int flow[4], swirl[4], heat[4];
     double uwx[4], uwy[4], omega[4], Tw[4];
     double scale;             // storage scale of the deviations (16-bit)
+    const float *ytab;        // device table: y[pitch] then 1/y[pitch] (FP64, rounded once)
 };
 
 struct Launch {

@@ -90,6 +90,8 @@ template <typename C> struct KP {
     int flow[4], swirl[4], heat[4];
     C uwx[4], uwy[4], omega[4], Tw[4];
     C scale, inv_scale;
+    C r0c, roc;           // inner and outer wall radii, rounded once
+    const float *ytab;    // y[pitch] then 1/y[pitch] (pair kernels)
     // Nusselt scales per side (diagnostics)
     double nu_scale[4];
 };
@@ -129,6 +131,9 @@ template <typename C> KP<C> make_kp(const HostParams &h)
     }
     k.scale = (C)h.scale;
     k.inv_scale = (C)(1.0 / h.scale);
+    k.r0c = (C)h.r0;
+    k.roc = (C)(h.r0 + h.nr);
+    k.ytab = h.ytab;
     // Nusselt normalisation (Sec. 3.2): lateral walls -R_w / (H dT), end
     // walls -(H / dT) * 2 / (R_o^2 - R_i^2); dT from the Dirichlet values.
     double tmin = 0, tmax = 0;
@@ -240,7 +245,7 @@ __device__ __forceinline__ C own(const S *__restrict__ src, const KP<C> &k, int 
 // psi on a rotating wall: rho0 * omega * radius
 template <typename C> __device__ __forceinline__ C wall_psi(const KP<C> &k, int side, C y)
 {
-    const C radius = side <= 1 ? y : (side == 2 ? (C)k.r0 : (C)(k.r0 + k.nr));
+    const C radius = side <= 1 ? y : (side == 2 ? k.r0c : k.roc);
     return k.rho0 * k.omega[side] * radius;
 }
 
@@ -1157,17 +1162,18 @@ size_t storage_bytes(int storage)
 Launch default_launch(const HostParams &p)
 {
     Launch l;
-    l.warps_per_block = p.storage == ST_FP64 ? 4 : 2;
+    l.warps_per_block = p.storage == ST_FP64 ? 4 : 1;
     l.use_tma = p.storage != ST_FP64 ? 1 : 0;
-    // 32-row segments (two halo rows per segment, 6 %), fewer when the
-    // lattice would otherwise leave SMs idle
+    // FP64: 32-row segments; pair kernels: 6-row segments (short segments
+    // balance the last wave; their halo rows are re-read from L2); fewer rows
+    // when the lattice would otherwise leave SMs idle
     const int nwin = p.storage == ST_FP64 ? nwindows(p.nr) : nwindows2(p.nr);
-    int seg = p.storage == ST_FP64 ? 32 : 8;
+    int seg = p.storage == ST_FP64 ? 32 : 6;
     const long long warps = (long long)nwin * ((p.nz + seg - 1) / seg);
     if (warps < 152LL * 16) {
         const long long segs = (152LL * 16 + nwin - 1) / nwin;
         seg = (int)((p.nz + segs - 1) / segs);
-        if (seg < 8) seg = 8;
+        if (seg < 6) seg = 6;
     }
     l.seg_rows = seg;
     return l;

@@ -511,9 +511,12 @@ __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__
     int hcol = lane == 0 ? c0 - 1 : c0 + 64;
     hcol = hcol < 0 ? 0 : (hcol >= nr ? nr - 1 : hcol);
     // radii and their inverses, computed in FP64 and rounded once
-    const double yAd = k.r0 + (A < nr ? A : nr - 1) + 0.5, yBd = k.r0 + (B < nr ? B : nr - 1) + 0.5;
-    const F2 y2 = mk2((float)yAd, (float)yBd);
-    const F2 iy = mk2((float)(1.0 / yAd), (float)(1.0 / yBd));
+    // y and 1/y of the pair from the table (FP64 on the host, rounded once;
+    // entries past nr - 1 repeat the last radius)
+    const float2 yv = *reinterpret_cast<const float2 *>(k.ytab + Ac);
+    const float2 iyv = *reinterpret_cast<const float2 *>(k.ytab + k.pitch + Ac);
+    const F2 y2 = mk2(yv.x, yv.y);
+    const F2 iy = mk2(iyv.x, iyv.y);
     const float sc = k.scale;
 
     F2 v[NQ];
@@ -684,13 +687,13 @@ __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__
                     Luy.v.x = 2.0f * k.uwy[sd] - uy;
                 }
                 const int sw = k.swirl[sd], ht = k.heat[sd];
-                Lut.v.x = sw == 2 ? -ut : (sw == 0 ? 2.0f * k.omega[sd] * (float)k.r0 - ut : ut);
+                Lut.v.x = sw == 2 ? -ut : (sw == 0 ? 2.0f * k.omega[sd] * k.r0c - ut : ut);
                 LT.v.x = ht == 0 ? 2.0f * k.Tw[sd] - T : T;
             }
             if (atAN || atBN) {
                 const int sd = 3;
                 const int sw = k.swirl[sd], ht = k.heat[sd];
-                const float Ro = (float)(k.r0 + k.nr);
+                const float Ro = k.roc;
                 if (atAN) {
                     const float ux = pm_cur.ux.v.x, uy = pm_cur.uy.v.x, ut = pm_cur.ut.v.x, T = pm_cur.T.v.x;
                     Rux.v.x = 2.0f * k.uwx[sd] - ux;
