@@ -56,6 +56,13 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def kernel_name(storage, row_fetch):
+    """The step kernel a launch configuration runs."""
+    if storage == "fp64":
+        return "k_step64"
+    return {1: "k_step2", 2: "k_step2_tma", 3: "k_step3_tma"}[row_fetch]
+
+
 def counters_for(key):
     """Per-launch DRAM traffic from the committed ncu summary, only while the
     kernel source still matches the one the counters were taken on."""
@@ -374,13 +381,16 @@ def main():
     bpn = BYTES_PER_NODE[args.storage]
     achieved = bpn * nodes / (ms_per_step * 1e-3) / 1e9  # GB/s of one launch
     peak = float(peaks["hbm_gbs"])
-    key = f"k_step_{args.storage}_{case.nr}x{case.nz}"
+    seg, wpb, fetch = g.get_launch()
+    kname = kernel_name(args.storage, fetch)
+    key = f"{kname}_{args.storage}_{case.nr}x{case.nz}"
     traffic = counters_for(key)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
-                "algorithmic_bytes_per_node": bpn, "kernel": "k_step (fused stream+source+collide)"}
+                "algorithmic_bytes_per_node": bpn,
+                "kernel": f"{kname} (fused stream + sources + collisions + boundaries, one launch per step)"}
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
@@ -388,6 +398,7 @@ def main():
             "dtype": DTYPE[args.storage], "data": "synthetic",
             "config": {"workload": workload_desc(case.nr, case.nz, args.storage), "nr": case.nr,
                        "nz": case.nz, "storage": args.storage, "parallelism": "replicas",
+                       "launch": {"seg_rows": seg, "warps_per_block": wpb, "row_fetch": fetch},
                        "l2": "inputs larger than L2 (working set %.0f MB)" % (2 * 19 * nodes *
                                                                           bpn / 38 / 1e6)},
             "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps,

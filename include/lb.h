@@ -187,8 +187,16 @@ LB_EXPORT lb_status lb_get_step(const lb_ctx *ctx, int64_t *step);
 /* Tune the launch: rows per z-segment of a warp (0 = automatic), warps per
  * block (0 = automatic, at most 8) and how the FP32 / 16-bit step fetches
  * its rows (0 = automatic, 1 = plain loads, 2 = TMA bulk tensor copies into
- * shared memory).  Results do not depend on the launch shape. */
+ * a shared-memory ring, 3 = the same ring holding rows i - 1, i, i + 1 of
+ * the step, read in place).  Results do not depend on the launch shape.
+ * LB_ERR_ARG for values out of range. */
 LB_EXPORT lb_status lb_set_launch(lb_ctx *ctx, int32_t seg_rows, int32_t warps_per_block, int32_t row_fetch);
+
+/* The launch the next lb_step uses, with the automatic choices resolved:
+ * rows per z-segment, warps per block and row fetch (1, 2 or 3 as for
+ * lb_set_launch; FP64 storage always 1).  NULL outputs are skipped. */
+LB_EXPORT lb_status lb_get_launch(const lb_ctx *ctx, int32_t *seg_rows, int32_t *warps_per_block,
+                                  int32_t *row_fetch);
 
 /* Diagnostics of a state held in the caller's device memory, with no context
  * and no scratch memory from the caller; the paper has no counterpart.

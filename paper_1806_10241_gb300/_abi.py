@@ -66,6 +66,7 @@ PROTOTYPES = {
     "lb_set_state": (_st, [_vp, _vp, C.c_size_t]),
     "lb_get_step": (_st, [_vp, C.POINTER(C.c_int64)]),
     "lb_set_launch": (_st, [_vp, C.c_int32, C.c_int32, C.c_int32]),
+    "lb_get_launch": (_st, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "lb_diagnostics_static": (_st, [C.POINTER(lb_grid_desc), C.POINTER(lb_params), _vp, C.c_int64, _vp,
                                     C.POINTER(lb_diag)]),
     "lb_batch_required_bytes": (_st, [C.c_int32, C.POINTER(C.c_size_t)]),

@@ -17,8 +17,8 @@ import torch
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 _lock = threading.Lock()
 
-SOLVER_CANDIDATES = [(8, 2, 2), (8, 4, 2), (16, 2, 2), (16, 4, 2), (32, 4, 2),
-                     (8, 2, 1), (8, 4, 1), (16, 4, 1), (32, 2, 1)]
+SOLVER_CANDIDATES = [(4, 1, 3), (4, 2, 3), (6, 1, 3), (8, 1, 3), (12, 2, 3), (16, 4, 3),
+                     (6, 1, 2), (8, 2, 2), (8, 2, 1), (16, 4, 1)]
 BATCH_CANDIDATES = [(8, 2), (8, 4), (16, 2), (16, 4), (32, 4)]
 
 
@@ -60,7 +60,7 @@ def tune_solver(solver, steps: int = 20, use_cache: bool = True) -> tuple:
         best = tuple(cache[key]["launch"])
         solver.set_launch(*best)
         return best
-    cands = SOLVER_CANDIDATES if solver.storage != "fp64" else [(s, w, 1) for s, w, _ in SOLVER_CANDIDATES[:5]]
+    cands = SOLVER_CANDIDATES if solver.storage != "fp64" else [(s, w, 1) for s in (16, 32) for w in (2, 4)]
     results = []
     for c in cands:
         solver.set_launch(*c)

@@ -484,15 +484,24 @@ lb_status lb_get_step(const lb_ctx *ctx, int64_t *step)
 lb_status lb_set_launch(lb_ctx *ctx, int32_t seg_rows, int32_t warps_per_block, int32_t row_fetch)
 {
     if (!ctx) return fail(nullptr, LB_ERR_ARG, "ctx is NULL");
-    if (seg_rows < 0 || warps_per_block < 0 || warps_per_block > 8 || row_fetch < 0 || row_fetch > 2)
-        return fail(ctx, LB_ERR_ARG, "seg_rows >= 0, 0 <= warps_per_block <= 8, 0 <= row_fetch <= 2");
+    if (seg_rows < 0 || warps_per_block < 0 || warps_per_block > 8 || row_fetch < 0 || row_fetch > 3)
+        return fail(ctx, LB_ERR_ARG, "seg_rows >= 0, 0 <= warps_per_block <= 8, 0 <= row_fetch <= 3");
     if (seg_rows && (ctx->hp.nz + seg_rows - 1) / seg_rows > 65535)
         return fail(ctx, LB_ERR_ARG, "seg_rows too small for nz (more than 65535 segments)");
     Launch d = lbk::default_launch(ctx->hp);
     ctx->launch.seg_rows = seg_rows ? seg_rows : d.seg_rows;
     ctx->launch.warps_per_block = warps_per_block ? warps_per_block : d.warps_per_block;
-    ctx->launch.use_tma = row_fetch == 0 ? d.use_tma : (row_fetch == 2 && ctx->hp.storage != LB_FP64 ? 1 : 0);
+    ctx->launch.use_tma = row_fetch == 0 ? d.use_tma : (row_fetch >= 2 && ctx->hp.storage != LB_FP64 ? row_fetch - 1 : 0);
     ctx->launch_auto = seg_rows == 0 && warps_per_block == 0 && row_fetch == 0;
+    return LB_OK;
+}
+
+lb_status lb_get_launch(const lb_ctx *ctx, int32_t *seg_rows, int32_t *warps_per_block, int32_t *row_fetch)
+{
+    if (!ctx) return fail(nullptr, LB_ERR_ARG, "ctx is NULL");
+    if (seg_rows) *seg_rows = ctx->launch.seg_rows;
+    if (warps_per_block) *warps_per_block = ctx->launch.warps_per_block;
+    if (row_fetch) *row_fetch = ctx->launch.use_tma + 1;
     return LB_OK;
 }
 

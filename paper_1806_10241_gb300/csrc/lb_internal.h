@@ -32,7 +32,7 @@ struct HostParams {
 struct Launch {
     int seg_rows;             // rows per z-segment
     int warps_per_block;
-    int use_tma;              // TMA row fetches (FP32 / 16-bit storage)
+    int use_tma;              // FP32 / 16-bit rows: 0 plain loads, 1 TMA ring, 2 TMA ring read in place
 };
 
 // One time step src -> dst; `step` seeds the stochastic rounding of 16-bit

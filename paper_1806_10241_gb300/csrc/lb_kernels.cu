@@ -741,6 +741,49 @@ __global__ void __maxnreg__(LB_STEP2_MAXREG)
     march2<S>(k, src, dst, warp * 64, s, e, salt, rs);
 }
 
+// The step with the rows resident in the TMA ring (march3): no row carried
+// in registers.  kRingStages<S> stages of one row each per warp.
+#ifndef LB_STEP3_MAXREG
+#define LB_STEP3_MAXREG 168
+#endif
+template <typename S> constexpr int kRingStages = sizeof(S) == 4 ? 3 : 4;
+
+template <typename S>
+size_t ring_smem_bytes(int wpb)
+{
+    return (size_t)wpb * (kRingStages<S> * TmaGeom<S>::stage_bytes + 128);
+}
+
+template <typename S>
+__global__ void __maxnreg__(LB_STEP3_MAXREG)
+    k_step3_tma(KP<float> k, const __grid_constant__ CUtensorMap map, const S *__restrict__ src,
+                S *__restrict__ dst, int seg_rows, int nwin2, uint32_t salt, int *status)
+{
+    constexpr int R = kRingStages<S>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int wib = threadIdx.x >> 5;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (warp >= nwin2) return;
+    const int s = blockIdx.y * seg_rows;
+    const int e = min(k.nz, s + seg_rows);
+    const bool has_m = s > 0 || k.xper, has_last = e < k.nz || k.xper;
+    const int per_warp = R * TmaGeom<S>::stage_bytes + 128;  // keeps every ring 128-byte aligned
+    unsigned char *ring = smem + per_warp * wib;
+    RowRing<S, R> rs;
+    rs.map = &map;
+    rs.ring = ring;
+    rs.ring_s = smem_u32(ring);
+    rs.bar_s = smem_u32(ring + R * TmaGeom<S>::stage_bytes);
+    rs.first = has_m ? s - 1 : s;
+    rs.nrows = (e - s) + (has_m ? 1 : 0) + (has_last ? 1 : 0);
+    rs.nz = k.nz;
+    rs.x0 = warp * 64 - TmaGeom<S>::off;
+    rs.lane = threadIdx.x & 31;
+    rs.status = status;
+    rs.start();
+    march3<S, R>(k, src, dst, warp * 64, s, e, salt, rs);
+}
+
 template <typename S, typename C>
 __global__ void __launch_bounds__(256) k_fields(KP<C> k, const S *__restrict__ src, double *__restrict__ out,
                                                 int row0, int row1, int nwin)
@@ -1099,7 +1142,18 @@ cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *
     } else {
         const int nwin2 = nwindows2(h.nr);
         dim3 grid((nwin2 + wpb - 1) / wpb, (h.nz + seg - 1) / seg);
-        if (tmap && l.use_tma) {
+        if (tmap && l.use_tma == 2) {
+            const size_t sm = ring_smem_bytes<S>(wpb);
+            static bool attr_set = false;
+            if (!attr_set) {
+                cudaError_t e = cudaFuncSetAttribute(k_step3_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)ring_smem_bytes<S>(8));
+                if (e != cudaSuccess) return e;
+                attr_set = true;
+            }
+            k_step3_tma<S><<<grid, 32 * wpb, sm, s>>>(k, *(const CUtensorMap *)tmap, (const S *)src, (S *)dst, seg,
+                                                       nwin2, step_salt(step), status);
+        } else if (tmap && l.use_tma) {
             const size_t sm = tma_smem_bytes<S>(wpb);
             static bool attr_set = false;
             if (!attr_set) {
@@ -1163,17 +1217,17 @@ Launch default_launch(const HostParams &p)
 {
     Launch l;
     l.warps_per_block = p.storage == ST_FP64 ? 4 : 1;
-    l.use_tma = p.storage != ST_FP64 ? 1 : 0;
-    // FP64: 32-row segments; pair kernels: 6-row segments (short segments
+    l.use_tma = p.storage != ST_FP64 ? 2 : 0;
+    // FP64: 32-row segments; pair kernels: 4-row segments (short segments
     // balance the last wave; their halo rows are re-read from L2); fewer rows
     // when the lattice would otherwise leave SMs idle
     const int nwin = p.storage == ST_FP64 ? nwindows(p.nr) : nwindows2(p.nr);
-    int seg = p.storage == ST_FP64 ? 32 : 6;
+    int seg = p.storage == ST_FP64 ? 32 : 4;
     const long long warps = (long long)nwin * ((p.nz + seg - 1) / seg);
     if (warps < 152LL * 16) {
         const long long segs = (152LL * 16 + nwin - 1) / nwin;
         seg = (int)((p.nz + segs - 1) / segs);
-        if (seg < 6) seg = 6;
+        if (seg < 4) seg = 4;
     }
     l.seg_rows = seg;
     return l;

@@ -496,28 +496,229 @@ template <typename S> struct RowTma {
     }
 };
 
+// Per-lane constants of a pair march.
+struct Lane2 {
+    int lane, A, Ac;
+    bool outA, atA0, atAN, atBN, edge_warp;
+    F2 y2, iy;
+};
+
+__device__ __forceinline__ Lane2 lane2(const KP<float> &k, int c0)
+{
+    Lane2 L;
+    L.lane = threadIdx.x & 31;
+    L.A = c0 + 2 * L.lane;
+    const int B = L.A + 1, nr = k.nr;
+    const int Amax = (nr - 1) & ~1;
+    L.Ac = L.A <= Amax ? L.A : Amax;  // even pair start inside the padded row
+    L.outA = L.A < nr;
+    L.atA0 = L.A == 0;
+    L.atAN = L.A == nr - 1;
+    L.atBN = B == nr - 1;
+    L.edge_warp = __any_sync(FULL, L.atA0 || L.atAN || L.atBN);
+    // y and 1/y of the pair from the table (FP64 on the host, rounded once;
+    // entries past nr - 1 repeat the last radius)
+    const float2 yv = *reinterpret_cast<const float2 *>(k.ytab + L.Ac);
+    const float2 iyv = *reinterpret_cast<const float2 *>(k.ytab + k.pitch + L.Ac);
+    L.y2 = mk2(yv.x, yv.y);
+    L.iy = mk2(iyv.x, iyv.y);
+    return L;
+}
+
+__device__ __forceinline__ void halo_fields(const KP<float> &k, const float h[NQ], float &ux, float &uy, float &ut,
+                                            float &T)
+{
+    const float rd = h[0] + h[1] + h[2] + h[3] + h[4] + h[5] + h[6] + h[7] + h[8];
+    const float ir = __fdividef(1.0f, k.rho0 + rd);
+    ux = (h[1] - h[3] + h[5] - h[6] - h[7] + h[8]) * ir;
+    uy = (h[2] - h[4] + h[5] + h[6] - h[7] - h[8]) * ir;
+    ut = (h[9] + h[10] + h[11] + h[12] + h[13]) * ir;
+    T = k.T0 + (h[14] + h[15] + h[16] + h[17] + h[18]);
+}
+
+// The rest of a row update once the pulled values of the pair are in fv, gv,
+// hv5: wall and axis rules (the own post-collision values they need are read
+// from src), central differences of the stored-state fields with ghosts, the
+// node update and the stores.
+template <typename S>
+__device__ __forceinline__ void row_tail(const KP<float> &k, const S *__restrict__ src, S *__restrict__ dst,
+                                         const Lane2 &L, int i, bool has_m, bool has_p, uint32_t salt, F2 fv[9],
+                                         F2 gv[5], F2 hv5[5], const PM2 &pm_cur, const PM2 &pm_n, F2 uy_prev,
+                                         float pmh_ux, float pmh_uy, float pmh_ut, float pmh_T)
+{
+    const int lane = L.lane, A = L.A, Ac = L.Ac, nz = k.nz;
+    const bool outA = L.outA, atA0 = L.atA0, atAN = L.atAN, atBN = L.atBN, edge_warp = L.edge_warp;
+    const F2 y2 = L.y2, iy = L.iy;
+    const float sc = k.scale;
+    // lateral boundaries: column 0 is always the x of a pair, column
+    // nr - 1 the x or the y
+    if (edge_warp) {
+        const float rw = k.rho0;
+        if (atA0) {
+            const int sd = 2;
+            if (k.flow[sd] == 1) {  // axis: mirror images
+                fv[2].v.x = own2<S>(src, k, 4, i, 0).v.x;
+                if (has_m) fv[5].v.x = own2<S>(src, k, 8, i > 0 ? i - 1 : nz - 1, 0).v.x;
+                if (has_p) fv[6].v.x = own2<S>(src, k, 7, i + 1 < nz ? i + 1 : 0, 0).v.x;
+            } else {
+                const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
+                fv[2].v.x = own2<S>(src, k, 4, i, 0).v.x + rw * (6.0f / 9.0f) * uy_w;
+                fv[5].v.x = own2<S>(src, k, 7, i, 0).v.x + rw * (6.0f / 36.0f) * (ux_w + uy_w);
+                fv[6].v.x = own2<S>(src, k, 8, i, 0).v.x + rw * (6.0f / 36.0f) * (-ux_w + uy_w);
+            }
+            gv[2].v.x = scalar_bc<float>(k.swirl[sd], own2<S>(src, k, G0 + 4, i, 0).v.x,
+                                         wall_psi<float>(k, sd, y2.v.x), true);
+            hv5[2].v.x = scalar_bc<float>(k.heat[sd], own2<S>(src, k, H0 + 4, i, 0).v.x, k.Tw[sd] - k.T0, false);
+        }
+        if (atAN || atBN) {
+            const int sd = 3;
+            const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
+            const F2 o2 = own2<S>(src, k, 2, i, Ac), o5 = own2<S>(src, k, 5, i, Ac), o6 = own2<S>(src, k, 6, i, Ac);
+            const F2 og = own2<S>(src, k, G0 + 2, i, Ac), oh = own2<S>(src, k, H0 + 2, i, Ac);
+            const float a4 = k.rho0 * (6.0f / 9.0f) * (-uy_w);
+            const float a7 = k.rho0 * (6.0f / 36.0f) * (-ux_w - uy_w);
+            const float a8 = k.rho0 * (6.0f / 36.0f) * (ux_w - uy_w);
+            const float psw = wall_psi<float>(k, sd, 0.0f), tw = k.Tw[sd] - k.T0;
+            if (atAN) {
+                fv[4].v.x = o2.v.x + a4;
+                fv[7].v.x = o5.v.x + a7;
+                fv[8].v.x = o6.v.x + a8;
+                gv[4].v.x = scalar_bc<float>(k.swirl[sd], og.v.x, psw, true);
+                hv5[4].v.x = scalar_bc<float>(k.heat[sd], oh.v.x, tw, false);
+            }
+            if (atBN) {
+                fv[4].v.y = o2.v.y + a4;
+                fv[7].v.y = o5.v.y + a7;
+                fv[8].v.y = o6.v.y + a8;
+                gv[4].v.y = scalar_bc<float>(k.swirl[sd], og.v.y, psw, true);
+                hv5[4].v.y = scalar_bc<float>(k.heat[sd], oh.v.y, tw, false);
+            }
+        }
+    }
+    // end walls; they win in corners
+    if (!has_m) {
+        const int sd = 0;
+        const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
+        fv[1] = own2<S>(src, k, 3, i, Ac) + sp(k.rho0 * (6.0f / 9.0f) * ux_w);
+        fv[5] = own2<S>(src, k, 7, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (ux_w + uy_w));
+        fv[8] = own2<S>(src, k, 6, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (ux_w - uy_w));
+        const F2 og = own2<S>(src, k, G0 + 3, i, Ac), oh = own2<S>(src, k, H0 + 3, i, Ac);
+        gv[1] = mk2(scalar_bc<float>(k.swirl[sd], og.v.x, wall_psi<float>(k, sd, y2.v.x), true),
+                    scalar_bc<float>(k.swirl[sd], og.v.y, wall_psi<float>(k, sd, y2.v.y), true));
+        hv5[1] = mk2(scalar_bc<float>(k.heat[sd], oh.v.x, k.Tw[sd] - k.T0, false),
+                     scalar_bc<float>(k.heat[sd], oh.v.y, k.Tw[sd] - k.T0, false));
+    }
+    if (!has_p) {
+        const int sd = 1;
+        const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
+        fv[3] = own2<S>(src, k, 1, i, Ac) + sp(k.rho0 * (6.0f / 9.0f) * (-ux_w));
+        fv[6] = own2<S>(src, k, 8, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (-ux_w + uy_w));
+        fv[7] = own2<S>(src, k, 5, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (-ux_w - uy_w));
+        const F2 og = own2<S>(src, k, G0 + 1, i, Ac), oh = own2<S>(src, k, H0 + 1, i, Ac);
+        gv[3] = mk2(scalar_bc<float>(k.swirl[sd], og.v.x, wall_psi<float>(k, sd, y2.v.x), true),
+                    scalar_bc<float>(k.swirl[sd], og.v.y, wall_psi<float>(k, sd, y2.v.y), true));
+        hv5[3] = mk2(scalar_bc<float>(k.heat[sd], oh.v.x, k.Tw[sd] - k.T0, false),
+                     scalar_bc<float>(k.heat[sd], oh.v.y, k.Tw[sd] - k.T0, false));
+    }
+
+    // central differences of the stored-state fields, with ghosts
+    const F2 uy_xm = has_m ? uy_prev : (sp(2.0f * k.uwy[0]) - pm_cur.uy);
+    const F2 uy_xp = has_p ? pm_n.uy : (sp(2.0f * k.uwy[1]) - pm_cur.uy);
+    float lux = __shfl_up_sync(FULL, pm_cur.ux.v.y, 1), luy = __shfl_up_sync(FULL, pm_cur.uy.v.y, 1);
+    float lut = __shfl_up_sync(FULL, pm_cur.ut.v.y, 1), lT = __shfl_up_sync(FULL, pm_cur.T.v.y, 1);
+    float rux = __shfl_down_sync(FULL, pm_cur.ux.v.x, 1), ruy = __shfl_down_sync(FULL, pm_cur.uy.v.x, 1);
+    float rut = __shfl_down_sync(FULL, pm_cur.ut.v.x, 1), rT = __shfl_down_sync(FULL, pm_cur.T.v.x, 1);
+    if (lane == 0) {
+        lux = pmh_ux;
+        luy = pmh_uy;
+        lut = pmh_ut;
+        lT = pmh_T;
+    }
+    if (lane == 31) {
+        rux = pmh_ux;
+        ruy = pmh_uy;
+        rut = pmh_ut;
+        rT = pmh_T;
+    }
+    F2 Lux = mk2(lux, pm_cur.ux.v.x), Luy = mk2(luy, pm_cur.uy.v.x);
+    F2 Lut = mk2(lut, pm_cur.ut.v.x), LT = mk2(lT, pm_cur.T.v.x);
+    F2 Rux = mk2(pm_cur.ux.v.y, rux), Ruy = mk2(pm_cur.uy.v.y, ruy);
+    F2 Rut = mk2(pm_cur.ut.v.y, rut), RT = mk2(pm_cur.T.v.y, rT);
+    if (edge_warp) {
+        if (atA0) {
+            const int sd = 2;
+            const float ux = pm_cur.ux.v.x, uy = pm_cur.uy.v.x, ut = pm_cur.ut.v.x, T = pm_cur.T.v.x;
+            if (k.flow[sd] == 1) {
+                Lux.v.x = ux;
+                Luy.v.x = -uy;
+            } else {
+                Lux.v.x = 2.0f * k.uwx[sd] - ux;
+                Luy.v.x = 2.0f * k.uwy[sd] - uy;
+            }
+            const int sw = k.swirl[sd], ht = k.heat[sd];
+            Lut.v.x = sw == 2 ? -ut : (sw == 0 ? 2.0f * k.omega[sd] * k.r0c - ut : ut);
+            LT.v.x = ht == 0 ? 2.0f * k.Tw[sd] - T : T;
+        }
+        if (atAN || atBN) {
+            const int sd = 3;
+            const int sw = k.swirl[sd], ht = k.heat[sd];
+            const float Ro = k.roc;
+            if (atAN) {
+                const float ux = pm_cur.ux.v.x, uy = pm_cur.uy.v.x, ut = pm_cur.ut.v.x, T = pm_cur.T.v.x;
+                Rux.v.x = 2.0f * k.uwx[sd] - ux;
+                Ruy.v.x = 2.0f * k.uwy[sd] - uy;
+                Rut.v.x = sw == 0 ? 2.0f * k.omega[sd] * Ro - ut : ut;
+                RT.v.x = ht == 0 ? 2.0f * k.Tw[sd] - T : T;
+            }
+            if (atBN) {
+                const float ux = pm_cur.ux.v.y, uy = pm_cur.uy.v.y, ut = pm_cur.ut.v.y, T = pm_cur.T.v.y;
+                Rux.v.y = 2.0f * k.uwx[sd] - ux;
+                Ruy.v.y = 2.0f * k.uwy[sd] - uy;
+                Rut.v.y = sw == 0 ? 2.0f * k.omega[sd] * Ro - ut : ut;
+                RT.v.y = ht == 0 ? 2.0f * k.Tw[sd] - T : T;
+            }
+        }
+    }
+    const F2 hf = sp(0.5f);
+    const F2 dxuy = (uy_xp - uy_xm) * hf;
+    const F2 dyux = (Rux - Lux) * hf;
+    const F2 dyuy = (Ruy - Luy) * hf;
+    const F2 dyut = (Rut - Lut) * hf;
+    const F2 dyT = (RT - LT) * hf;
+
+    NodeOut2 o;
+    update_node2(k, iy, fv, gv, hv5, dxuy, dyux, dyuy, dyut, dyT, o);
+
+    if (outA) {
+        S *p = dst + (long long)i * k.pitch + A;
+        uint32_t w = 0;
+        if (PairIO<S>::rounds) w = pcg_hash((uint32_t)(i * k.pitch + A) ^ salt) | 1u;
+        const F2 m = sp(Scaled<S>::value ? sc : 1.0f);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            if (PairIO<S>::rounds) w = xorshift32(w);
+            PairIO<S>::st(p + q * k.plane, Scaled<S>::value ? o.f[q] * m : o.f[q], w);
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            if (PairIO<S>::rounds) w = xorshift32(w);
+            PairIO<S>::st(p + (G0 + q) * k.plane, Scaled<S>::value ? o.g[q] * m : o.g[q], w);
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            if (PairIO<S>::rounds) w = xorshift32(w);
+            PairIO<S>::st(p + (H0 + q) * k.plane, Scaled<S>::value ? o.h[q] * m : o.h[q], w);
+        }
+    }
+
+}
+
 template <typename S, typename RS>
 __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__ src, S *__restrict__ dst, int c0,
                                        int row_s, int row_e, uint32_t salt, RS &rs)
 {
-    const int lane = threadIdx.x & 31;
-    const int nr = k.nr, nz = k.nz;
-    const int A = c0 + 2 * lane, B = A + 1;
-    const int Amax = (nr - 1) & ~1;
-    const int Ac = A <= Amax ? A : Amax;  // even pair start inside the padded row
-    const bool outA = A < nr;
-    const bool atA0 = A == 0, atAN = A == nr - 1, atBN = B == nr - 1;
-    const bool edge_warp = __any_sync(FULL, atA0 || atAN || atBN);
-    int hcol = lane == 0 ? c0 - 1 : c0 + 64;
-    hcol = hcol < 0 ? 0 : (hcol >= nr ? nr - 1 : hcol);
-    // radii and their inverses, computed in FP64 and rounded once
-    // y and 1/y of the pair from the table (FP64 on the host, rounded once;
-    // entries past nr - 1 repeat the last radius)
-    const float2 yv = *reinterpret_cast<const float2 *>(k.ytab + Ac);
-    const float2 iyv = *reinterpret_cast<const float2 *>(k.ytab + k.pitch + Ac);
-    const F2 y2 = mk2(yv.x, yv.y);
-    const F2 iy = mk2(iyv.x, iyv.y);
-    const float sc = k.scale;
+    const Lane2 L = lane2(k, c0);
+    const int lane = L.lane, nz = k.nz;
 
     F2 v[NQ];
     float hv[NQ];
@@ -526,15 +727,6 @@ __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__
     float pmh_ux, pmh_uy, pmh_ut, pmh_T;  // halo column fields (lanes 0 / 31)
     F2 uy_prev = sp(0.0f);
     bool has_m;
-
-    auto halo_fields = [&](const float h[NQ], float &ux, float &uy, float &ut, float &T) {
-        const float rd = h[0] + h[1] + h[2] + h[3] + h[4] + h[5] + h[6] + h[7] + h[8];
-        const float ir = __fdividef(1.0f, k.rho0 + rd);
-        ux = (h[1] - h[3] + h[5] - h[6] - h[7] + h[8]) * ir;
-        uy = (h[2] - h[4] + h[5] + h[6] - h[7] - h[8]) * ir;
-        ut = (h[9] + h[10] + h[11] + h[12] + h[13]) * ir;
-        T = k.T0 + (h[14] + h[15] + h[16] + h[17] + h[18]);
-    };
 
     if (row_s > 0 || k.xper) {
         if (!rs.get(v, hv)) return rs.finish();
@@ -552,7 +744,7 @@ __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__
         F2 xpt[5];
         groups2(v, hv, lane, xm_cur, x0_cur, xpt);
         pm_cur = moments2(v, k);
-        halo_fields(hv, pmh_ux, pmh_uy, pmh_ut, pmh_T);
+        halo_fields(k, hv, pmh_ux, pmh_uy, pmh_ut, pmh_T);
     }
 
     for (int i = row_s; i < row_e; ++i) {
@@ -564,7 +756,7 @@ __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__
             if (!rs.get(v, hv)) return rs.finish();
             groups2(v, hv, lane, xm_n, x0_n, xp_n);
             pm_n = moments2(v, k);
-            halo_fields(hv, nh_ux, nh_uy, nh_ut, nh_T);
+            halo_fields(k, hv, nh_ux, nh_uy, nh_ut, nh_T);
         } else {
 #pragma unroll
             for (int q = 0; q < 5; ++q) xp_n[q] = xm_n[q] = sp(0.0f);
@@ -581,166 +773,8 @@ __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__
         hv5[0] = x0_cur[6]; hv5[2] = x0_cur[7]; hv5[4] = x0_cur[8];
         fv[3] = xp_n[0]; fv[6] = xp_n[1]; fv[7] = xp_n[2]; gv[3] = xp_n[3]; hv5[3] = xp_n[4];
 
-        // lateral boundaries: column 0 is always the x of a pair, column
-        // nr - 1 the x or the y
-        if (edge_warp) {
-            const float rw = k.rho0;
-            if (atA0) {
-                const int sd = 2;
-                if (k.flow[sd] == 1) {  // axis: mirror images
-                    fv[2].v.x = own2<S>(src, k, 4, i, 0).v.x;
-                    if (has_m) fv[5].v.x = own2<S>(src, k, 8, i > 0 ? i - 1 : nz - 1, 0).v.x;
-                    if (has_p) fv[6].v.x = own2<S>(src, k, 7, i + 1 < nz ? i + 1 : 0, 0).v.x;
-                } else {
-                    const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
-                    fv[2].v.x = own2<S>(src, k, 4, i, 0).v.x + rw * (6.0f / 9.0f) * uy_w;
-                    fv[5].v.x = own2<S>(src, k, 7, i, 0).v.x + rw * (6.0f / 36.0f) * (ux_w + uy_w);
-                    fv[6].v.x = own2<S>(src, k, 8, i, 0).v.x + rw * (6.0f / 36.0f) * (-ux_w + uy_w);
-                }
-                gv[2].v.x = scalar_bc<float>(k.swirl[sd], own2<S>(src, k, G0 + 4, i, 0).v.x,
-                                             wall_psi<float>(k, sd, y2.v.x), true);
-                hv5[2].v.x = scalar_bc<float>(k.heat[sd], own2<S>(src, k, H0 + 4, i, 0).v.x, k.Tw[sd] - k.T0, false);
-            }
-            if (atAN || atBN) {
-                const int sd = 3;
-                const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
-                const F2 o2 = own2<S>(src, k, 2, i, Ac), o5 = own2<S>(src, k, 5, i, Ac), o6 = own2<S>(src, k, 6, i, Ac);
-                const F2 og = own2<S>(src, k, G0 + 2, i, Ac), oh = own2<S>(src, k, H0 + 2, i, Ac);
-                const float a4 = k.rho0 * (6.0f / 9.0f) * (-uy_w);
-                const float a7 = k.rho0 * (6.0f / 36.0f) * (-ux_w - uy_w);
-                const float a8 = k.rho0 * (6.0f / 36.0f) * (ux_w - uy_w);
-                const float psw = wall_psi<float>(k, sd, 0.0f), tw = k.Tw[sd] - k.T0;
-                if (atAN) {
-                    fv[4].v.x = o2.v.x + a4;
-                    fv[7].v.x = o5.v.x + a7;
-                    fv[8].v.x = o6.v.x + a8;
-                    gv[4].v.x = scalar_bc<float>(k.swirl[sd], og.v.x, psw, true);
-                    hv5[4].v.x = scalar_bc<float>(k.heat[sd], oh.v.x, tw, false);
-                }
-                if (atBN) {
-                    fv[4].v.y = o2.v.y + a4;
-                    fv[7].v.y = o5.v.y + a7;
-                    fv[8].v.y = o6.v.y + a8;
-                    gv[4].v.y = scalar_bc<float>(k.swirl[sd], og.v.y, psw, true);
-                    hv5[4].v.y = scalar_bc<float>(k.heat[sd], oh.v.y, tw, false);
-                }
-            }
-        }
-        // end walls; they win in corners
-        if (!has_m) {
-            const int sd = 0;
-            const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
-            fv[1] = own2<S>(src, k, 3, i, Ac) + sp(k.rho0 * (6.0f / 9.0f) * ux_w);
-            fv[5] = own2<S>(src, k, 7, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (ux_w + uy_w));
-            fv[8] = own2<S>(src, k, 6, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (ux_w - uy_w));
-            const F2 og = own2<S>(src, k, G0 + 3, i, Ac), oh = own2<S>(src, k, H0 + 3, i, Ac);
-            gv[1] = mk2(scalar_bc<float>(k.swirl[sd], og.v.x, wall_psi<float>(k, sd, y2.v.x), true),
-                        scalar_bc<float>(k.swirl[sd], og.v.y, wall_psi<float>(k, sd, y2.v.y), true));
-            hv5[1] = mk2(scalar_bc<float>(k.heat[sd], oh.v.x, k.Tw[sd] - k.T0, false),
-                         scalar_bc<float>(k.heat[sd], oh.v.y, k.Tw[sd] - k.T0, false));
-        }
-        if (!has_p) {
-            const int sd = 1;
-            const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
-            fv[3] = own2<S>(src, k, 1, i, Ac) + sp(k.rho0 * (6.0f / 9.0f) * (-ux_w));
-            fv[6] = own2<S>(src, k, 8, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (-ux_w + uy_w));
-            fv[7] = own2<S>(src, k, 5, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (-ux_w - uy_w));
-            const F2 og = own2<S>(src, k, G0 + 1, i, Ac), oh = own2<S>(src, k, H0 + 1, i, Ac);
-            gv[3] = mk2(scalar_bc<float>(k.swirl[sd], og.v.x, wall_psi<float>(k, sd, y2.v.x), true),
-                        scalar_bc<float>(k.swirl[sd], og.v.y, wall_psi<float>(k, sd, y2.v.y), true));
-            hv5[3] = mk2(scalar_bc<float>(k.heat[sd], oh.v.x, k.Tw[sd] - k.T0, false),
-                         scalar_bc<float>(k.heat[sd], oh.v.y, k.Tw[sd] - k.T0, false));
-        }
-
-        // central differences of the stored-state fields, with ghosts
-        const F2 uy_xm = has_m ? uy_prev : (sp(2.0f * k.uwy[0]) - pm_cur.uy);
-        const F2 uy_xp = has_p ? pm_n.uy : (sp(2.0f * k.uwy[1]) - pm_cur.uy);
-        float lux = __shfl_up_sync(FULL, pm_cur.ux.v.y, 1), luy = __shfl_up_sync(FULL, pm_cur.uy.v.y, 1);
-        float lut = __shfl_up_sync(FULL, pm_cur.ut.v.y, 1), lT = __shfl_up_sync(FULL, pm_cur.T.v.y, 1);
-        float rux = __shfl_down_sync(FULL, pm_cur.ux.v.x, 1), ruy = __shfl_down_sync(FULL, pm_cur.uy.v.x, 1);
-        float rut = __shfl_down_sync(FULL, pm_cur.ut.v.x, 1), rT = __shfl_down_sync(FULL, pm_cur.T.v.x, 1);
-        if (lane == 0) {
-            lux = pmh_ux;
-            luy = pmh_uy;
-            lut = pmh_ut;
-            lT = pmh_T;
-        }
-        if (lane == 31) {
-            rux = pmh_ux;
-            ruy = pmh_uy;
-            rut = pmh_ut;
-            rT = pmh_T;
-        }
-        F2 Lux = mk2(lux, pm_cur.ux.v.x), Luy = mk2(luy, pm_cur.uy.v.x);
-        F2 Lut = mk2(lut, pm_cur.ut.v.x), LT = mk2(lT, pm_cur.T.v.x);
-        F2 Rux = mk2(pm_cur.ux.v.y, rux), Ruy = mk2(pm_cur.uy.v.y, ruy);
-        F2 Rut = mk2(pm_cur.ut.v.y, rut), RT = mk2(pm_cur.T.v.y, rT);
-        if (edge_warp) {
-            if (atA0) {
-                const int sd = 2;
-                const float ux = pm_cur.ux.v.x, uy = pm_cur.uy.v.x, ut = pm_cur.ut.v.x, T = pm_cur.T.v.x;
-                if (k.flow[sd] == 1) {
-                    Lux.v.x = ux;
-                    Luy.v.x = -uy;
-                } else {
-                    Lux.v.x = 2.0f * k.uwx[sd] - ux;
-                    Luy.v.x = 2.0f * k.uwy[sd] - uy;
-                }
-                const int sw = k.swirl[sd], ht = k.heat[sd];
-                Lut.v.x = sw == 2 ? -ut : (sw == 0 ? 2.0f * k.omega[sd] * k.r0c - ut : ut);
-                LT.v.x = ht == 0 ? 2.0f * k.Tw[sd] - T : T;
-            }
-            if (atAN || atBN) {
-                const int sd = 3;
-                const int sw = k.swirl[sd], ht = k.heat[sd];
-                const float Ro = k.roc;
-                if (atAN) {
-                    const float ux = pm_cur.ux.v.x, uy = pm_cur.uy.v.x, ut = pm_cur.ut.v.x, T = pm_cur.T.v.x;
-                    Rux.v.x = 2.0f * k.uwx[sd] - ux;
-                    Ruy.v.x = 2.0f * k.uwy[sd] - uy;
-                    Rut.v.x = sw == 0 ? 2.0f * k.omega[sd] * Ro - ut : ut;
-                    RT.v.x = ht == 0 ? 2.0f * k.Tw[sd] - T : T;
-                }
-                if (atBN) {
-                    const float ux = pm_cur.ux.v.y, uy = pm_cur.uy.v.y, ut = pm_cur.ut.v.y, T = pm_cur.T.v.y;
-                    Rux.v.y = 2.0f * k.uwx[sd] - ux;
-                    Ruy.v.y = 2.0f * k.uwy[sd] - uy;
-                    Rut.v.y = sw == 0 ? 2.0f * k.omega[sd] * Ro - ut : ut;
-                    RT.v.y = ht == 0 ? 2.0f * k.Tw[sd] - T : T;
-                }
-            }
-        }
-        const F2 hf = sp(0.5f);
-        const F2 dxuy = (uy_xp - uy_xm) * hf;
-        const F2 dyux = (Rux - Lux) * hf;
-        const F2 dyuy = (Ruy - Luy) * hf;
-        const F2 dyut = (Rut - Lut) * hf;
-        const F2 dyT = (RT - LT) * hf;
-
-        NodeOut2 o;
-        update_node2(k, iy, fv, gv, hv5, dxuy, dyux, dyuy, dyut, dyT, o);
-
-        if (outA) {
-            S *p = dst + (long long)i * k.pitch + A;
-            uint32_t w = 0;
-            if (PairIO<S>::rounds) w = pcg_hash((uint32_t)(i * k.pitch + A) ^ salt) | 1u;
-            const F2 m = sp(Scaled<S>::value ? sc : 1.0f);
-#pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                if (PairIO<S>::rounds) w = xorshift32(w);
-                PairIO<S>::st(p + q * k.plane, Scaled<S>::value ? o.f[q] * m : o.f[q], w);
-            }
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                if (PairIO<S>::rounds) w = xorshift32(w);
-                PairIO<S>::st(p + (G0 + q) * k.plane, Scaled<S>::value ? o.g[q] * m : o.g[q], w);
-            }
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                if (PairIO<S>::rounds) w = xorshift32(w);
-                PairIO<S>::st(p + (H0 + q) * k.plane, Scaled<S>::value ? o.h[q] * m : o.h[q], w);
-            }
-        }
+        row_tail<S>(k, src, dst, L, i, has_m, has_p, salt, fv, gv, hv5, pm_cur, pm_n, uy_prev, pmh_ux, pmh_uy,
+                    pmh_ut, pmh_T);
 
         // rotate the row window
 #pragma unroll
@@ -757,5 +791,237 @@ __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__
         pmh_ut = nh_ut;
         pmh_T = nh_T;
         has_m = true;
+    }
+}
+
+// ---- the march with the rows resident in shared memory ------------------------
+//
+// The same row update with no row carried in registers: the TMA ring keeps
+// the rows i - 1, i and i + 1 of the step in shared memory and the pulled
+// values are read straight from them, the radial shift being a column offset
+// (the stage holds the two halo columns).  Row i - 1 is released once its
+// e_x = +1 group is read, so that the copy of row i + 2 is in flight during
+// the step.  R stages (R >= 3) per warp.
+
+template <typename S, int R> struct RowRing {
+    static_assert(R >= 3, "rows i - 1, i and i + 1 must fit");
+    const CUtensorMap *map;
+    const unsigned char *ring;  // this warp's stages
+    uint32_t ring_s, bar_s;     // shared addresses of the stages and of the barriers
+    int first, nrows, nz, x0, lane, waited, issued;
+    int *status;
+
+    __device__ __forceinline__ void issue(int t)
+    {
+        int row = first + t;
+        row = row >= nz ? row - nz : (row < 0 ? row + nz : row);
+        const int st = t % R;
+        const uint32_t bar = bar_s + 8u * st, dst = ring_s + (uint32_t)(TmaGeom<S>::stage_bytes * st);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((uint32_t)TmaGeom<S>::box_bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];" ::"r"(dst),
+            "l"((unsigned long long)map), "r"(x0), "r"(row), "r"(0), "r"(bar)
+            : "memory");
+    }
+
+    __device__ __forceinline__ void start()
+    {
+        waited = 0;
+        issued = nrows < R ? nrows : R;
+        if (lane == 0) {
+            for (int s = 0; s < R; ++s)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s + 8u * s) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            for (int t = 0; t < issued; ++t) issue(t);
+        }
+        __syncwarp();
+    }
+
+    __device__ __forceinline__ bool wait_one(int t)
+    {
+        const uint32_t bar = bar_s + 8u * (t % R), parity = (uint32_t)((t / R) & 1);
+        uint32_t ok = 0;
+        for (int it = 0; it < kTmaWaitLimit && !ok; ++it)
+            asm volatile(
+                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                : "=r"(ok)
+                : "r"(bar), "r"(parity)
+                : "memory");
+        return ok != 0;
+    }
+
+    // rows up to sequence index t have landed (false after a timeout, with
+    // the status word set)
+    __device__ __forceinline__ bool wait_upto(int t)
+    {
+        bool ok = true;
+        while (waited <= t) {
+            if (!wait_one(waited)) {
+                ok = false;
+                break;
+            }
+            ++waited;
+        }
+        if (!__all_sync(FULL, ok)) {
+            if (lane == 0) atomicExch(status, (int)LB_ERR_TIMEOUT);
+            return false;
+        }
+        return true;
+    }
+
+    __device__ __forceinline__ const S *stage(int t) const
+    {
+        return reinterpret_cast<const S *>(ring + TmaGeom<S>::stage_bytes * (t % R));
+    }
+
+    // every lane is done with row t: its stage takes row t + R
+    __device__ __forceinline__ void release(int t)
+    {
+        __syncwarp();
+        if (t + R < nrows) {
+            if (lane == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(t + R);
+            }
+            issued = t + R + 1;
+        }
+    }
+
+    // after an error: give the copies still in flight a bounded wait
+    __device__ __forceinline__ void finish()
+    {
+        for (int t = waited; t < issued; ++t) (void)wait_one(t);
+    }
+};
+
+// stage reads: the pair (A, B), the pair shifted one column left (A - 1, A)
+// or right (B, B + 1), and one column (the halo lanes)
+template <typename S> struct StageRd {
+    const S *b;
+    int cA;  // column of A inside the stage
+    float is;
+    __device__ __forceinline__ F2 scl(F2 v) const { return Scaled<S>::value ? v * sp(is) : v; }
+    __device__ __forceinline__ F2 pair(int q) const
+    {
+        return scl(PairIO<S>::ld(b + q * TmaGeom<S>::cols + cA));
+    }
+    __device__ __forceinline__ F2 left(int q) const
+    {
+        const S *p = b + q * TmaGeom<S>::cols + cA;
+        return scl(mk2(Cvt<S, float>::ld(p - 1), Cvt<S, float>::ld(p)));
+    }
+    __device__ __forceinline__ F2 right(int q) const
+    {
+        const S *p = b + q * TmaGeom<S>::cols + cA;
+        return scl(mk2(Cvt<S, float>::ld(p + 1), Cvt<S, float>::ld(p + 2)));
+    }
+    __device__ __forceinline__ float col(int q, int c) const
+    {
+        const float v = Cvt<S, float>::ld(b + q * TmaGeom<S>::cols + c);
+        return Scaled<S>::value ? v * is : v;
+    }
+};
+
+template <typename S, int R>
+__device__ __forceinline__ void march3(const KP<float> &k, const S *__restrict__ src, S *__restrict__ dst, int c0,
+                                       int row_s, int row_e, uint32_t salt, RowRing<S, R> &rs)
+{
+    const Lane2 L = lane2(k, c0);
+    const int lane = L.lane, nz = k.nz;
+    constexpr int O = TmaGeom<S>::off;
+    const int hc = lane == 0 ? O - 1 : O + 64;  // halo column of lanes 0 / 31
+    const int first = (row_s > 0 || k.xper) ? row_s - 1 : row_s;
+    StageRd<S> rd{nullptr, O + 2 * lane, k.inv_scale};
+
+    // stored-state fields of row row_s (and u_y of row row_s - 1)
+    PM2 pm_cur;
+    float pmh_ux, pmh_uy, pmh_ut, pmh_T;
+    F2 uy_prev = sp(0.0f);
+    {
+        if (!rs.wait_upto(row_s - first)) return rs.finish();
+        F2 v[NQ];
+        float hv[NQ];
+        if (row_s > first) {
+            rd.b = rs.stage(0);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) v[q] = rd.pair(q);
+            uy_prev = moments2(v, k).uy;
+        }
+        rd.b = rs.stage(row_s - first);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            v[q] = rd.pair(q);
+            hv[q] = rd.col(q, hc);
+        }
+        pm_cur = moments2(v, k);
+        halo_fields(k, hv, pmh_ux, pmh_uy, pmh_ut, pmh_T);
+    }
+
+    for (int i = row_s; i < row_e; ++i) {
+        const bool has_m = i > 0 || k.xper;
+        const bool has_p = (i + 1 < nz) || k.xper;
+        const int t = i - first;
+        if (has_p && !rs.wait_upto(t + 1)) return rs.finish();
+
+        F2 fv[9], gv[5], hv5[5];
+        // e_x = +1 group from row i - 1, then that row's stage is free
+        if (has_m) {
+            rd.b = rs.stage(t - 1);
+            fv[1] = rd.pair(1);
+            fv[5] = rd.left(5);
+            fv[8] = rd.right(8);
+            gv[1] = rd.pair(G0 + 1);
+            hv5[1] = rd.pair(H0 + 1);
+            rs.release(t - 1);
+        } else {
+            fv[1] = fv[5] = fv[8] = gv[1] = hv5[1] = sp(0.0f);
+        }
+        // e_x = 0 group from row i
+        rd.b = rs.stage(t);
+        fv[0] = rd.pair(0);
+        fv[2] = rd.left(2);
+        fv[4] = rd.right(4);
+        gv[0] = rd.pair(G0 + 0);
+        gv[2] = rd.left(G0 + 2);
+        gv[4] = rd.right(G0 + 4);
+        hv5[0] = rd.pair(H0 + 0);
+        hv5[2] = rd.left(H0 + 2);
+        hv5[4] = rd.right(H0 + 4);
+        // e_x = -1 group and the stored-state fields of row i + 1
+        PM2 pm_n;
+        float nh_ux = 0, nh_uy = 0, nh_ut = 0, nh_T = 0;
+        if (has_p) {
+            rd.b = rs.stage(t + 1);
+            F2 v[NQ];
+            float hv[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                v[q] = rd.pair(q);
+                hv[q] = rd.col(q, hc);
+            }
+            pm_n = moments2(v, k);
+            halo_fields(k, hv, nh_ux, nh_uy, nh_ut, nh_T);
+            fv[3] = v[3];
+            fv[6] = rd.left(6);
+            fv[7] = rd.right(7);
+            gv[3] = v[G0 + 3];
+            hv5[3] = v[H0 + 3];
+        } else {
+            fv[3] = fv[6] = fv[7] = gv[3] = hv5[3] = sp(0.0f);
+            pm_n = pm_cur;
+        }
+
+        row_tail<S>(k, src, dst, L, i, has_m, has_p, salt, fv, gv, hv5, pm_cur, pm_n, uy_prev, pmh_ux, pmh_uy,
+                    pmh_ut, pmh_T);
+
+        uy_prev = pm_cur.uy;
+        pm_cur = pm_n;
+        pmh_ux = nh_ux;
+        pmh_uy = nh_uy;
+        pmh_ut = nh_ut;
+        pmh_T = nh_T;
     }
 }

@@ -80,8 +80,15 @@ class Solver:
 
     # -- the ABI --------------------------------------------------------------
     def set_launch(self, seg_rows: int = 0, warps_per_block: int = 0, row_fetch: int = 0) -> None:
-        """row_fetch: 0 automatic, 1 plain loads, 2 TMA (FP32 / 16-bit storage)."""
+        """row_fetch: 0 automatic, 1 plain loads, 2 TMA ring, 3 TMA ring with
+        the rows read in place (FP32 / 16-bit storage)."""
         self._check(self.L.lb_set_launch(self.ctx, int(seg_rows), int(warps_per_block), int(row_fetch)))
+
+    def get_launch(self) -> tuple:
+        """(seg_rows, warps_per_block, row_fetch) the next step uses."""
+        s, w, f = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(self.L.lb_get_launch(self.ctx, C.byref(s), C.byref(w), C.byref(f)))
+        return s.value, w.value, f.value
 
     def init_fields(self, fields: np.ndarray) -> None:
         a = np.ascontiguousarray(fields, np.float64).reshape(5, self.nz, self.nr)

@@ -27,8 +27,12 @@ def _cases():
     return cs
 
 
+@pytest.mark.parametrize("row_fetch", [1, 2, 3])
 @pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
-def test_batch_equals_individual_runs(storage):
+def test_batch_equals_individual_runs(storage, row_fetch):
+    """The batched step and the single-lattice step with each row fetch give
+    the same bits (16-bit storage included: the rounding draws depend only on
+    the node, the plane and the step)."""
     from paper_1806_10241_gb300.batch import Batch
     from paper_1806_10241_gb300.solver import Solver
     stream = torch.cuda.Stream()
@@ -36,6 +40,7 @@ def test_batch_equals_individual_runs(storage):
     alone = []
     for c in cases:
         s = Solver(c.params, storage=storage, stream=stream)
+        s.set_launch(0, 0, row_fetch)
         s.init_fields(c.fields)
         s.step(37)
         alone.append(s.get_dist())

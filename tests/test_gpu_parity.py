@@ -127,7 +127,8 @@ def test_fp64_distributions_match_oracle(name, nr, nz):
 def test_fp32_distributions_match_oracle(name, nr, nz):
     params = BUILDERS[name](nr, nz)
     st = random_state(params, seed=7 + nr * 1000 + nz)
-    for steps, launch in ((1, (0, 0)), (5, (4, 2))):
+    # default launch, then each row fetch (plain loads, TMA ring, TMA ring read in place)
+    for steps, launch in ((1, (0, 0, 0)), (5, (4, 2, 1)), (5, (5, 1, 2)), (5, (3, 2, 3))):
         got, want, _, _ = run_both(params, st, steps, "fp32", launch)
         err = np.max(np.abs(got - want))
         assert err < 2e-6, (name, nr, nz, steps, err)
@@ -179,7 +180,8 @@ def test_launch_shape_does_not_change_results():
     params = cylinder_axis(97, 70)
     st = random_state(params, seed=5)
     ref = None
-    for launch in ((0, 0), (1, 1), (7, 2), (70, 4), (16, 8)):
+    for launch in ((0, 0, 0), (1, 1, 1), (7, 2, 1), (70, 4, 2), (16, 8, 2), (1, 1, 3), (6, 1, 3), (70, 4, 3),
+                   (16, 8, 3)):
         got, _, _, _ = run_both(params, st, 4, "fp32", launch)
         if ref is None:
             ref = got
