@@ -227,6 +227,69 @@ def run_serving(args):
     return 0
 
 
+def run_precision(args):
+    """--workload precision: the 16-bit storage forms of the benchmark
+    cylinder.  MLUPS of each storage at 1024 x 2048, the errors of FP32, FP16
+    and BF16 against the GPU FP64 path at full size, and against the FP64
+    oracle on a 256 x 512 copy (Re = 1000 on R)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_1806_10241_gb300 import workloads as W
+    from paper_1806_10241_gb300.solver import Solver
+    torch.cuda.set_device(0)
+
+    def rel_l2(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    def errors(f, d, fr, dr):
+        e = {fld: rel_l2(f[q], fr[q]) for q, fld in ((1, "u_z"), (2, "u_r"), (3, "u_theta"), (4, "T"))}
+        e["nu_avg"] = abs(d["nu_avg"] - dr["nu_avg"]) / abs(dr["nu_avg"])
+        return {k: float("%.3g" % v) for k, v in e.items()}
+
+    steps = args.prec_steps
+    case = W.config_cylinder(args.nr, args.nz)
+    nodes = case.nr * case.nz
+    res, mlups = {}, {}
+    for storage in ("fp64", "fp32", "fp16", "bf16"):
+        g = Solver(case.params, storage=storage)
+        g.init_fields(case.fields)
+        g.step(3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(g.stream)
+        g.step(steps - 3)
+        e1.record(g.stream)
+        e1.synchronize()
+        mlups[storage] = round(nodes * (steps - 3) / (e0.elapsed_time(e1) * 1e3), 1)
+        res[storage] = (g.fields(), g.diag())
+        del g
+        torch.cuda.empty_cache()
+    full = {s: errors(*res[s], *res["fp64"]) for s in ("fp32", "fp16", "bf16")}
+    small = W.swirling_cylinder(nr=256, nz=512, Re=1000.0, Ra=1e5, Pr=0.7, u_lid=0.05, amp=1e-6, seed=0)
+    o = oracle.Oracle(small.params)
+    o.init_fields(small.fields)
+    o.step(args.prec_oracle_steps)
+    ref = (o.fields(), o.diag())
+    copy = {}
+    for storage in ("fp32", "fp16", "bf16"):
+        g = Solver(small.params, storage=storage)
+        g.init_fields(small.fields)
+        g.step(args.prec_oracle_steps)
+        copy[storage] = errors(g.fields(), g.diag(), *ref)
+    line = {"metric": METRIC, "value": mlups["fp16"], "unit": "MLUPS", "n_gpus": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE["fp16"], "data": "synthetic",
+            "config": {"workload": workload_desc(case.nr, case.nz, "fp16/bf16/fp32/fp64"), "steps": steps},
+            "mlups": mlups,
+            "speedup_vs_fp32": {s: round(mlups[s] / mlups["fp32"], 3) for s in ("fp16", "bf16")},
+            "rel_err_vs_gpu_fp64_full_size": full,
+            "rel_err_vs_oracle_256x512": {"steps": args.prec_oracle_steps, **copy},
+            "nu_avg": {s: res[s][1]["nu_avg"] for s in res}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     """--impl reference: the oracle timed on the host cores, K steps after W
     warm-up steps, each step a bounded slab of the workload."""
@@ -282,7 +345,9 @@ def main():
     ap.add_argument("--nr", type=int, default=1024)
     ap.add_argument("--nz", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "serving"])
+    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "serving", "precision"])
+    ap.add_argument("--prec-steps", dest="prec_steps", type=int, default=2000)
+    ap.add_argument("--prec-oracle-steps", dest="prec_oracle_steps", type=int, default=1500)
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--nr-lo", dest="nr_lo", type=int, default=64)
     ap.add_argument("--nr-hi", dest="nr_hi", type=int, default=128)
@@ -296,6 +361,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "precision":
+        return run_precision(args)
 
     import numpy as np
     import torch
