@@ -10,8 +10,11 @@ replayed from a CUDA graph).  Between rounds it
     steps and retires the ones that reached the steady state
     (|Nu(t) - Nu(t - window)| < tol), hit the step cap or diverged,
   * rebuilds the batch when its membership changed.
-Latency of a request = finish time - arrival time.  `run_sequential` serves
-the same stream one plain solve at a time, for comparison.
+A request whose lattice can never fit the budget is rejected; `cancel(rid)`
+withdraws a request (pending: dropped; active: retired at the end of the
+round).  Latency of a request = finish time - arrival time.
+`run_sequential` serves the same stream one plain solve at a time, for
+comparison.
 """
 from __future__ import annotations
 
@@ -37,7 +40,7 @@ class Record:
     finished: float = -1.0
     steps: int = 0
     nu: float = float("nan")
-    status: str = "pending"  # converged | capped | diverged
+    status: str = "pending"  # converged | capped | diverged | rejected | cancelled
 
     @property
     def latency(self) -> float:
@@ -53,14 +56,17 @@ class Report:
 
     def summary(self) -> dict:
         done = [r for r in self.records if r.finished >= 0]
-        lat = np.array([r.latency for r in done]) if done else np.array([np.nan])
+        solved = [r for r in done if r.status in ("converged", "capped", "diverged")]
+        lat = np.array([r.latency for r in solved]) if solved else np.array([np.nan])
         ok = [r for r in done if r.status == "converged"]
-        steps_nodes = sum(r.steps * r.nodes for r in done)
+        steps_nodes = sum(r.steps * r.nodes for r in solved)
         return {"mode": self.mode, "requests": len(self.records), "completed": len(done),
                 "converged": len(ok), "capped": sum(r.status == "capped" for r in done),
                 "diverged": sum(r.status == "diverged" for r in done),
+                "rejected": sum(r.status == "rejected" for r in done),
+                "cancelled": sum(r.status == "cancelled" for r in done),
                 "makespan_s": round(self.makespan, 3),
-                "solves_per_s": round(len(done) / self.makespan, 3) if self.makespan > 0 else None,
+                "solves_per_s": round(len(solved) / self.makespan, 3) if self.makespan > 0 else None,
                 "p50_latency_s": round(float(np.percentile(lat, 50)), 3),
                 "p99_latency_s": round(float(np.percentile(lat, 99)), 3),
                 "MLUPS": round(steps_nodes / self.makespan / 1e6, 1) if self.makespan > 0 else None,
@@ -108,6 +114,11 @@ class Server:
         free, _ = torch.cuda.mem_get_info(self.device)
         self.budget = (free - reserve_bytes) if hbm_budget is None else int(hbm_budget)
         self.stream = torch.cuda.Stream(self.device)
+        self._cancelled: set[int] = set()
+
+    def cancel(self, rid: int) -> None:
+        """Withdraw request rid (takes effect at the next round boundary)."""
+        self._cancelled.add(rid)
 
     # -- one request's admission and retirement ---------------------------------------
     def _admit(self, req: Request, now: float, rec: Record) -> _Active:
@@ -133,7 +144,8 @@ class Server:
             return True
         return False
 
-    def run(self, requests: list[Request], clock=time.perf_counter) -> Report:
+    def run(self, requests: list[Request], clock=time.perf_counter, on_round=None) -> Report:
+        """Serve the stream; on_round(server, now) is called after every round."""
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         records = {r.rid: Record(r.rid, r.case.name, r.case.nr * r.case.nz, r.arrival) for r in requests}
         active: list[_Active] = []
@@ -144,14 +156,25 @@ class Server:
         rounds = 0
         while pending or active:
             now = clock() - t0
+            # withdrawn requests that are still waiting
+            if self._cancelled and pending:
+                keep = deque()
+                for req in pending:
+                    if req.rid in self._cancelled:
+                        rec = records[req.rid]
+                        rec.status, rec.finished = "cancelled", now
+                    else:
+                        keep.append(req)
+                pending = keep
             # admit what has arrived, in arrival order, while it fits
             while pending and pending[0].arrival <= now and len(active) < self.max_active:
                 need = required_bytes(pending[0].case.params, self.storage)
+                if need > self.budget:  # can never fit: reject
+                    req = pending.popleft()
+                    rec = records[req.rid]
+                    rec.status, rec.finished = "rejected", clock() - t0
+                    continue
                 if used + need > self.budget:
-                    if not active:  # can never fit: reject
-                        req = pending.popleft()
-                        rec = records[req.rid]
-                        rec.status, rec.finished = "rejected", clock() - t0
                     break
                 req = pending.popleft()
                 active.append(self._admit(req, now, records[req.rid]))
@@ -172,9 +195,15 @@ class Server:
             rounds += 1
             # every lattice of the batch has taken the same number of rounds
             # since its admission; check those at a multiple of check_every
+            if on_round is not None:
+                on_round(self, clock() - t0)
             finished = []
             for a in active:
-                if a.solver.step_count % self.check_every == 0 and self._check(a):
+                if a.rec.rid in self._cancelled:
+                    a.rec.steps = a.solver.step_count
+                    a.rec.status = "cancelled"
+                    finished.append(a)
+                elif a.solver.step_count % self.check_every == 0 and self._check(a):
                     finished.append(a)
             if finished:
                 now = clock() - t0

@@ -77,3 +77,58 @@ def test_sequential_baseline_runs():
     rep = srv.run_sequential(reqs, storage="fp32")
     s = rep.summary()
     assert s["completed"] == 3 and s["p99_latency_s"] >= s["p50_latency_s"]
+
+
+def test_oversize_request_is_rejected_and_the_rest_complete():
+    from paper_1806_10241_gb300.serving import Server
+    from paper_1806_10241_gb300.solver import required_bytes
+    reqs = [W.Request(r.rid, 0.0, r.case) for r in _stream(3)]
+    biggest = max(required_bytes(r.case.params, "fp16") for r in reqs)
+    huge = W.annulus_convection(nr=2048, nz=4096, Ra=1e4)
+    reqs.append(W.Request(99, 0.0, huge))
+    assert required_bytes(huge.params, "fp16") > 2 * biggest + 1
+    srv = Server(storage="fp16", steps_per_round=100, check_every=200, window=400, tol=1e-7, max_steps=400,
+                 hbm_budget=2 * biggest + 1)
+    rep = srv.run(reqs)
+    st = {r.rid: r.status for r in rep.records}
+    assert st[99] == "rejected"
+    assert all(st[r.rid] in ("converged", "capped") for r in reqs[:3])
+    s = rep.summary()
+    assert s["rejected"] == 1 and s["completed"] == 4
+
+
+def test_cancelled_requests_leave_the_batch():
+    from paper_1806_10241_gb300.serving import Server
+    reqs = [W.Request(r.rid, 0.0, r.case) for r in _stream(4)]
+    srv = Server(storage="fp16", steps_per_round=100, check_every=200, window=400, tol=1e-9, max_steps=1000,
+                 max_active=2)
+
+    def on_round(server, now):
+        server.cancel(0)  # active from the first round
+        server.cancel(3)  # still waiting for a slot
+
+    rep = srv.run(reqs, on_round=on_round)
+    st = {r.rid: r for r in rep.records}
+    assert st[0].status == "cancelled" and st[0].steps == 100
+    assert st[3].status == "cancelled" and st[3].admitted < 0
+    assert st[1].status in ("converged", "capped") and st[2].status in ("converged", "capped")
+    assert rep.summary()["cancelled"] == 2
+
+
+def test_diverged_lattice_is_reported_and_retired():
+    from paper_1806_10241_gb300 import _abi
+    from paper_1806_10241_gb300.serving import Server
+    from paper_1806_10241_gb300.solver import Solver
+    bad = W.annulus_convection(nr=24, nz=24, Ra=1e4, seed=1)
+    bad.fields = bad.fields.copy()
+    bad.fields[4, 5, 7] = np.nan  # a NaN temperature in the request's initial state
+    s = Solver(bad.params, storage="fp32")
+    s.init_fields(bad.fields)
+    s.step(5)
+    assert s.diag()["status"] == _abi.LB_ERR_DIVERGED
+    reqs = [W.Request(0, 0.0, bad)] + [W.Request(r.rid + 1, 0.0, r.case) for r in _stream(2)]
+    srv = Server(storage="fp16", steps_per_round=100, check_every=200, window=400, tol=1e-7, max_steps=400)
+    rep = srv.run(reqs)
+    st = {r.rid: r.status for r in rep.records}
+    assert st[0] == "diverged"
+    assert st[1] in ("converged", "capped") and st[2] in ("converged", "capped")
