@@ -50,7 +50,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("lb_kernels.cu", "lb_internal.h"):
+    for name in ("lb_kernels.cu", "lb_internal.h", "lb_pair.cuh"):
         with open(os.path.join(ROOT, "paper_1806_10241_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

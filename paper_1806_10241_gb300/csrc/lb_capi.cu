@@ -148,6 +148,7 @@ lb_status need_params(lb_ctx *ctx)
 Launch diag_launch(const lb_ctx *ctx)
 {
     Launch l = ctx->launch;
+    if (l.seg_rows < 32) l.seg_rows = 32;  // the diagnostics march: longer segments, fewer partial sums
     const long long nwin = (ctx->hp.nr + 29) / 30;
     const long long bx = (nwin + 3) / 4;
     long long segs = (ctx->hp.nz + l.seg_rows - 1) / l.seg_rows;

@@ -784,6 +784,8 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG)
     march3<S, R>(k, src, dst, warp * 64, s, e, salt, rs);
 }
 
+constexpr int kFieldRows = 32;  // rows per z-segment of the field export
+
 template <typename S, typename C>
 __global__ void __launch_bounds__(256) k_fields(KP<C> k, const S *__restrict__ src, double *__restrict__ out,
                                                 int row0, int row1, int nwin)
@@ -791,7 +793,8 @@ __global__ void __launch_bounds__(256) k_fields(KP<C> k, const S *__restrict__ s
     const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (warp >= nwin) return;
     const int c = warp * OUT_COLS - 1 + (threadIdx.x & 31);
-    march<S, C, MODE_FIELDS>(k, src, nullptr, out, row0, c, row0, row1, nullptr);
+    const int s = row0 + blockIdx.y * kFieldRows, e = min(row1, s + kFieldRows);
+    march<S, C, MODE_FIELDS>(k, src, nullptr, out, row0, c, s, e, nullptr);
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -940,16 +943,30 @@ __global__ void __launch_bounds__(256) k_wall_strip(KP<C> k, const double *__res
     }
 }
 
-__global__ void k_diag_final(const double *__restrict__ partial, int nblocks, double *__restrict__ result)
+// One block of 256 threads: per sum, strided partial sums in a fixed order,
+// then a fixed tree (deterministic for a given number of blocks).
+__global__ void __launch_bounds__(256) k_diag_final(const double *__restrict__ partial, int nblocks,
+                                                    double *__restrict__ result)
 {
-    const int q = threadIdx.x;
-    if (q >= NSUM || (q >= 4 && q < 8)) return;  // 4..7: wall sums (k_wall)
-    double r = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
-        const double v = partial[b * NSUM + q];
-        r = (q == 3 || q == 8) ? fmax(r, v) : r + v;
+    __shared__ double sh[256];
+    for (int q = 0; q < NSUM; ++q) {
+        if (q >= 4 && q < 8) continue;  // 4..7: wall sums (k_wall)
+        const bool mx = q == 3 || q == 8;
+        double r = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+            const double v = partial[b * NSUM + q];
+            r = mx ? fmax(r, v) : r + v;
+        }
+        sh[threadIdx.x] = r;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) sh[threadIdx.x] = mx ? fmax(sh[threadIdx.x], sh[threadIdx.x + w])
+                                                            : sh[threadIdx.x] + sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) result[q] = sh[0];
+        __syncthreads();
     }
-    result[q] = r;
 }
 
 // ---- initialisation and exchange ---------------------------------------------
@@ -1178,7 +1195,7 @@ cudaError_t fields_t(const HostParams &h, const Launch &l, const void *src, doub
     const KP<C> k = make_kp<C>(h);
     const int nwin = nwindows(h.nr);
     const int wpb = l.warps_per_block;
-    dim3 grid((nwin + wpb - 1) / wpb, 1);
+    dim3 grid((nwin + wpb - 1) / wpb, (row1 - row0 + kFieldRows - 1) / kFieldRows);
     k_fields<S, C><<<grid, 32 * wpb, 0, s>>>(k, (const S *)src, out, row0, row1, nwin);
     return cudaGetLastError();
 }
@@ -1195,7 +1212,7 @@ cudaError_t diag_t(const HostParams &h, const Launch &l, const void *src, double
     const int nb = grid.x * grid.y;
     if (nb > MAX_DIAG_BLOCKS) return cudaErrorInvalidValue;
     k_diag<S, C><<<grid, 32 * wpb, 0, s>>>(k, (const S *)src, partial, tfield, seg, nwin);
-    k_diag_final<<<1, 32, 0, s>>>(partial, nb, result);
+    k_diag_final<<<1, 256, 0, s>>>(partial, nb, result);
     k_wall<C><<<1, 256, 0, s>>>(k, tfield, result);
     return cudaGetLastError();
 }
@@ -1432,7 +1449,7 @@ cudaError_t diag_static_t(const HostParams &h, const Launch &l, const void *src,
     dim3 grid((nwin + 3) / 4, (h.nz + l.seg_rows - 1) / l.seg_rows);
     double *result = scratch, *partial = scratch + 16, *strips = scratch + 16 + (size_t)nb * NSUM;
     k_diag_strip<S, C><<<grid, 128, 0, s>>>(k, (const S *)src, partial, strips, l.seg_rows, nwin);
-    k_diag_final<<<1, 32, 0, s>>>(partial, nb, result);
+    k_diag_final<<<1, 256, 0, s>>>(partial, nb, result);
     k_wall_strip<C><<<1, 256, 0, s>>>(k, strips, result);
     return cudaGetLastError();
 }
@@ -1493,6 +1510,7 @@ extern "C" lb_status lb_diagnostics_static(const lb_grid_desc *desc, const lb_pa
     }
     // launch shape within the static scratch: at most kScratchMaxBlocks blocks
     Launch l = default_launch(h);
+    if (l.seg_rows < 32) l.seg_rows = 32;  // as lb_diagnostics
     const long long bx = (nwindows(h.nr) + 3) / 4;
     long long segs = (h.nz + l.seg_rows - 1) / l.seg_rows;
     if (bx * segs > kScratchMaxBlocks) {
