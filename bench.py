@@ -227,6 +227,82 @@ def run_serving(args):
     return 0
 
 
+def run_batch(args):
+    """--workload batch: 256 uneven annulus-convection lattices (nr, nz ~
+    U{32..512}, seeds 0..255) advanced together by the batched step, replayed
+    from CUDA graphs; aggregate MLUPS and HBM roofline, and the Nu of the
+    smallest instances against the oracle after the same steps."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_1806_10241_gb300 import autotune
+    from paper_1806_10241_gb300 import workloads as W
+    from paper_1806_10241_gb300.batch import Batch
+    from paper_1806_10241_gb300.solver import Solver
+    torch.cuda.set_device(0)
+    storage = args.batch_storage
+    cases = W.batched_instances(args.instances)
+    stream = torch.cuda.Stream()
+    solvers = []
+    for cs in cases:
+        s = Solver(cs.params, storage=storage, stream=stream)
+        s.init_fields(cs.fields)
+        solvers.append(s)
+    nodes = sum(cs.nr * cs.nz for cs in cases)
+    b = Batch(solvers, stream=stream, graph_steps=args.graph_steps)
+    launch = autotune.tune_batch(b, graph_steps=args.graph_steps)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.6)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    t1 = time.time()
+    clocks.stop()
+    ms = e0.elapsed_time(e1)
+    value = nodes * args.steps / (ms * 1e3)
+    peaks, peak_kind = measured_peaks()
+    bpn = BYTES_PER_NODE[storage]
+    achieved = bpn * nodes * args.steps / (ms * 1e-3) / 1e9
+    # Nu of the smallest instances against the oracle (same steps from the same state)
+    order = sorted(range(len(cases)), key=lambda m: cases[m].nr * cases[m].nz)
+    pick = [m for m in order if cases[m].nr <= 64 and cases[m].nz <= 64] or order[:args.oracle_instances]
+    nu = []
+    for m in pick[:args.oracle_instances]:
+        cs = cases[m]
+        o = oracle.Oracle(cs.params)
+        o.init_fields(cs.fields)
+        o.step(solvers[m].step_count)
+        dn, do = solvers[m].diag(), o.diag()
+        nu.append({"instance": m, "nr": cs.nr, "nz": cs.nz, "steps": solvers[m].step_count,
+                   "nu_gpu": dn["nu_avg"], "nu_oracle": do["nu_avg"],
+                   "rel_err": abs(dn["nu_avg"] - do["nu_avg"]) / abs(do["nu_avg"])})
+    b.close()
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[storage], "data": "synthetic",
+            "config": {"workload": f"{len(cases)} annulus-convection lattices, nr, nz ~ U{{32..512}}, "
+                                   "R_o/R_i ~ U[1.5,3], Ra log-U[1e3,1e5], inner swirl ~ U[0,0.05], seeds 0..",
+                       "nodes": nodes, "storage": storage,
+                       "launch": {"seg_rows": launch[0], "warps_per_block": launch[1], "row_fetch": launch[2],
+                                  "graph_steps": args.graph_steps},
+                       "l2": "inputs larger than L2 (working set %.0f MB)" % (bpn * nodes / 1e6)},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": float(peaks["hbm_gbs"]),
+                         "unit": "GB/s", "frac": round(achieved / float(peaks["hbm_gbs"]), 4), "traffic": None,
+                         "peak_kind": peak_kind, "algorithmic_bytes_per_node": bpn,
+                         "kernel": "k_batch3 (batched fused step)"},
+            "gpu_launches": args.steps, "clocks": clocks.summary(t0, t1), "nu_vs_oracle": nu}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_precision(args):
     """--workload precision: the 16-bit storage forms of the benchmark
     cylinder.  MLUPS of each storage at 1024 x 2048, the errors of FP32, FP16
@@ -345,7 +421,11 @@ def main():
     ap.add_argument("--nr", type=int, default=1024)
     ap.add_argument("--nz", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "serving", "precision"])
+    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "serving", "precision", "batch"])
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--batch-storage", dest="batch_storage", default="fp16", choices=["fp16", "bf16", "fp32"])
+    ap.add_argument("--graph-steps", dest="graph_steps", type=int, default=10)
+    ap.add_argument("--oracle-instances", dest="oracle_instances", type=int, default=3)
     ap.add_argument("--prec-steps", dest="prec_steps", type=int, default=2000)
     ap.add_argument("--prec-oracle-steps", dest="prec_oracle_steps", type=int, default=1500)
     ap.add_argument("--requests", type=int, default=40)
@@ -363,6 +443,8 @@ def main():
         return run_serving(args)
     if args.workload == "precision":
         return run_precision(args)
+    if args.workload == "batch":
+        return run_batch(args)
 
     import numpy as np
     import torch

@@ -226,9 +226,10 @@ LB_EXPORT lb_status lb_diagnostics_static(const lb_grid_desc *desc, const lb_par
 
 /* ---- batches: many lattices advanced together --------------------------------
  * A batch advances a set of FP32 or 16-bit lattices (any shapes, any
- * parameters) with one persistent kernel launch per step over all their
- * 64-column x z-segment tiles, replayed from a CUDA graph of graph_steps
- * launches when the stream is not the legacy default stream.  Each lattice's
+ * parameters) with one kernel launch per step over all their 64-column x
+ * z-segment tiles (work items numbered by a prefix sum over the lattices),
+ * replayed from a CUDA graph of graph_steps launches when the stream is not
+ * the legacy default stream.  Each lattice's
  * update is the one lb_step performs (same arithmetic, same rounding bits).
  * While a batch exists its lattices are stepped through it only; their step
  * counters and current buffers follow the batch, so lb_diagnostics and the
@@ -239,9 +240,11 @@ LB_EXPORT lb_status lb_batch_required_bytes(int32_t n, size_t *bytes);
 LB_EXPORT lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_buf, size_t bytes, void *cuda_stream,
                                     lb_batch **out);
 /* rows per z-segment (0 = keep), warps per block (0 = keep), launches per
- * CUDA graph (0 or 1 = no graph) */
+ * CUDA graph (0 or 1 = no graph), row fetch (0 = keep, 1 = plain loads on a
+ * persistent grid, 3 = TMA ring read in place, one warp per work item; the
+ * default is 3).  LB_ERR_ARG for values out of range. */
 LB_EXPORT lb_status lb_batch_set_launch(lb_batch *b, int32_t seg_rows, int32_t warps_per_block,
-                                        int32_t graph_steps);
+                                        int32_t graph_steps, int32_t row_fetch);
 LB_EXPORT lb_status lb_batch_step(lb_batch *b, int32_t nsteps);
 LB_EXPORT lb_status lb_batch_destroy(lb_batch *b);
 

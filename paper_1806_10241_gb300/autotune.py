@@ -19,7 +19,7 @@ _lock = threading.Lock()
 
 SOLVER_CANDIDATES = [(4, 1, 3), (4, 2, 3), (6, 1, 3), (8, 1, 3), (12, 2, 3), (16, 4, 3),
                      (6, 1, 2), (8, 2, 2), (8, 2, 1), (16, 4, 1)]
-BATCH_CANDIDATES = [(8, 2), (8, 4), (16, 2), (16, 4), (32, 4)]
+BATCH_CANDIDATES = [(4, 1, 3), (4, 2, 3), (6, 1, 3), (8, 1, 3), (8, 2, 1), (16, 4, 1)]
 
 
 def _size_class(n: int) -> int:
@@ -77,22 +77,22 @@ def tune_solver(solver, steps: int = 20, use_cache: bool = True) -> tuple:
 
 
 def tune_batch(batch, steps: int = 10, graph_steps: int = 10, use_cache: bool = True) -> tuple:
-    """Pick (seg_rows, warps_per_block) for a batch, keyed by its node count."""
+    """Pick (seg_rows, warps_per_block, row_fetch) for a batch, keyed by its node count."""
     key = f"batch/{batch.solvers[0].storage}/{_size_class(batch.nodes)}/{len(batch.solvers)}"
     with _lock:
         cache = _load() if use_cache else {}
-    if key in cache:
+    if key in cache and len(cache[key]["launch"]) == 3:
         best = tuple(cache[key]["launch"])
-        batch.set_launch(best[0], best[1], graph_steps)
+        batch.set_launch(best[0], best[1], graph_steps, best[2])
         return best
     results = []
-    for seg, wpb in BATCH_CANDIDATES:
-        batch.set_launch(seg, wpb, 0)
+    for seg, wpb, fetch in BATCH_CANDIDATES:
+        batch.set_launch(seg, wpb, 0, fetch)
         batch.step(2)
-        results.append((_time(batch.stream, batch.step, steps), (seg, wpb)))
+        results.append((_time(batch.stream, batch.step, steps), (seg, wpb, fetch)))
     results.sort()
     best = results[0][1]
-    batch.set_launch(best[0], best[1], graph_steps)
+    batch.set_launch(best[0], best[1], graph_steps, best[2])
     with _lock:
         cache = _load()
         cache[key] = {"launch": list(best), "ms_per_step": results[0][0]}

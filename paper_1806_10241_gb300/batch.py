@@ -1,8 +1,8 @@
 """Many lattices advanced together through the C ABI batch calls.
 
 All lattices of a batch share the storage type (FP32 or 16-bit); their
-shapes and parameters may differ.  One persistent kernel launch per step
-covers every tile of every lattice, replayed from a CUDA graph.
+shapes and parameters may differ.  One kernel launch per step covers every
+tile of every lattice, replayed from a CUDA graph.
 """
 from __future__ import annotations
 
@@ -16,7 +16,7 @@ from .solver import Solver
 
 class Batch:
     def __init__(self, solvers: list[Solver], stream: torch.cuda.Stream | None = None,
-                 seg_rows: int = 0, warps_per_block: int = 0, graph_steps: int = 8):
+                 seg_rows: int = 0, warps_per_block: int = 0, graph_steps: int = 8, row_fetch: int = 0):
         if not solvers:
             raise ValueError("empty batch")
         self.L = _abi.load()
@@ -31,10 +31,13 @@ class Batch:
         _abi.check(self.L.lb_batch_create(arr, n, C.c_void_p(self.buffer.data_ptr()), self.buffer.numel(),
                                           C.c_void_p(self.stream.cuda_stream), C.byref(h)))
         self.h = h
-        self.set_launch(seg_rows, warps_per_block, graph_steps)
+        self.set_launch(seg_rows, warps_per_block, graph_steps, row_fetch)
 
-    def set_launch(self, seg_rows: int = 0, warps_per_block: int = 0, graph_steps: int = 8) -> None:
-        _abi.check(self.L.lb_batch_set_launch(self.h, int(seg_rows), int(warps_per_block), int(graph_steps)))
+    def set_launch(self, seg_rows: int = 0, warps_per_block: int = 0, graph_steps: int = 8,
+                   row_fetch: int = 0) -> None:
+        """row_fetch: 0 keep, 1 plain loads, 3 TMA ring read in place."""
+        _abi.check(self.L.lb_batch_set_launch(self.h, int(seg_rows), int(warps_per_block), int(graph_steps),
+                                              int(row_fetch)))
 
     def step(self, n: int = 1) -> None:
         _abi.check(self.L.lb_batch_step(self.h, int(n)))

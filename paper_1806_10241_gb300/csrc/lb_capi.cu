@@ -527,7 +527,7 @@ struct lb_batch {
     int *d_prefix;
     void *d_ctl;
     cudaStream_t stream;
-    int seg_rows, wpb, blocks, total, graph_steps;
+    int seg_rows, wpb, blocks, total, graph_steps, row_fetch;
     unsigned long long counter;
     cudaGraphExec_t gexec;
     bool graph_valid;
@@ -553,8 +553,9 @@ static lb_status batch_upload(lb_batch *b)
     b->hprefix.assign((size_t)n + 1, 0);
     for (int m = 0; m < n; ++m) {
         lb_ctx *c = b->ctxs[m];
-        lbk::batch_fill_desc(c->hp, c->dist[0], c->dist[1], b->step0[m], b->parity0[m], b->seg_rows,
-                             b->hdesc.data() + (size_t)m * db);
+        cudaError_t e = lbk::batch_fill_desc(c->hp, c->dist[0], c->dist[1], b->step0[m], b->parity0[m],
+                                             b->seg_rows, c->status, b->hdesc.data() + (size_t)m * db);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch descriptor (tensor map)");
         b->hprefix[m + 1] = b->hprefix[m] + lbk::batch_items(c->hp, b->seg_rows);
     }
     b->total = b->hprefix[n];
@@ -610,13 +611,15 @@ lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_buf, size_t 
     b->d_prefix = (int *)(b->buf + poff);
     b->d_ctl = b->buf + coff;
     b->stream = (cudaStream_t)cuda_stream;
-    b->seg_rows = 8;
-    b->wpb = 2;
+    b->seg_rows = 4;
+    b->wpb = 1;
     b->graph_steps = 8;
+    b->row_fetch = 3;
     b->counter = 0;
     b->graph_valid = false;
     b->blocks = lbk::batch_grid(storage, b->wpb);
-    cudaError_t e = cudaMemsetAsync(b->d_ctl, 0, lbk::batch_ctl_bytes(), b->stream);
+    cudaError_t e = lbk::batch_prepare(storage);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctl, 0, lbk::batch_ctl_bytes(), b->stream);
     if (e != cudaSuccess) {
         delete b;
         return cuda_fail(nullptr, e, "batch reset");
@@ -630,10 +633,14 @@ lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_buf, size_t 
     return LB_OK;
 }
 
-lb_status lb_batch_set_launch(lb_batch *b, int32_t seg_rows, int32_t warps_per_block, int32_t graph_steps)
+lb_status lb_batch_set_launch(lb_batch *b, int32_t seg_rows, int32_t warps_per_block, int32_t graph_steps,
+                              int32_t row_fetch)
 {
-    if (!b || seg_rows < 0 || warps_per_block < 0 || warps_per_block > 8 || graph_steps < 0)
-        return fail(nullptr, LB_ERR_ARG, "seg_rows >= 0, 0 <= warps_per_block <= 8, graph_steps >= 0");
+    if (!b || seg_rows < 0 || warps_per_block < 0 || warps_per_block > 8 || graph_steps < 0 ||
+        !(row_fetch == 0 || row_fetch == 1 || row_fetch == 3))
+        return fail(nullptr, LB_ERR_ARG,
+                    "seg_rows >= 0, 0 <= warps_per_block <= 8, graph_steps >= 0, row_fetch 0, 1 or 3");
+    if (row_fetch) b->row_fetch = row_fetch;
     if (seg_rows) b->seg_rows = seg_rows;
     if (warps_per_block) {
         b->wpb = warps_per_block;
@@ -652,7 +659,7 @@ lb_status lb_batch_step(lb_batch *b, int32_t nsteps)
         cudaGraph_t g;
         cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
         for (int t = 0; e == cudaSuccess && t < b->graph_steps; ++t)
-            e = lbk::launch_batch(b->storage, b->d_desc, b->d_prefix, (int)b->ctxs.size(), b->total, b->d_ctl,
+            e = lbk::launch_batch(b->storage, b->row_fetch, b->d_desc, b->d_prefix, (int)b->ctxs.size(), b->total, b->d_ctl,
                                   b->wpb, b->blocks, b->stream);
         cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
         if (e == cudaSuccess) e = e2;
@@ -669,7 +676,7 @@ lb_status lb_batch_step(lb_batch *b, int32_t nsteps)
             if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch graph launch");
         }
     for (; left > 0; --left) {
-        cudaError_t e = lbk::launch_batch(b->storage, b->d_desc, b->d_prefix, (int)b->ctxs.size(), b->total,
+        cudaError_t e = lbk::launch_batch(b->storage, b->row_fetch, b->d_desc, b->d_prefix, (int)b->ctxs.size(), b->total,
                                           b->d_ctl, b->wpb, b->blocks, b->stream);
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch launch");
     }

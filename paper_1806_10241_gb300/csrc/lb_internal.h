@@ -66,11 +66,18 @@ size_t storage_bytes(int storage);
 size_t batch_desc_bytes();
 size_t batch_ctl_bytes();
 int batch_items(const HostParams &h, int seg_rows);
-void batch_fill_desc(const HostParams &h, void *buf0, void *buf1, unsigned long long step0, int parity0,
-                     int seg_rows, void *out);
+// One lattice's descriptor: parameters, both buffers and their TMA tensor
+// maps, the step count and current buffer when the batch was made, and the
+// lattice's device status word (bounded-wait timeouts).
+cudaError_t batch_fill_desc(const HostParams &h, void *buf0, void *buf1, unsigned long long step0, int parity0,
+                            int seg_rows, int *status, void *out);
 int batch_grid(int storage, int wpb);
-cudaError_t launch_batch(int storage, const void *desc, const int *prefix, int n, int total, void *ctl, int wpb,
-                         int blocks, cudaStream_t s);
+// Kernel attributes of the batched step; called before any stream capture.
+cudaError_t batch_prepare(int storage);
+// row_fetch: 1 plain loads (persistent grid of `blocks`), 3 TMA ring read in
+// place (one warp per work item).
+cudaError_t launch_batch(int storage, int row_fetch, const void *desc, const int *prefix, int n, int total,
+                         void *ctl, int wpb, int blocks, cudaStream_t s);
 // Message for lb_last_error(NULL) on this thread.
 void set_global_error(const char *msg);
 Launch default_launch(const HostParams &p);

@@ -1065,9 +1065,11 @@ __host__ __device__ __forceinline__ uint32_t salt_of(unsigned long long step)
     return (uint32_t)(z ^ (z >> 31));
 }
 
-struct BatchDesc {
+struct alignas(128) BatchDesc {
+    unsigned char map[2][128];  // CUtensorMap of buf[0], buf[1] (64-byte aligned in the device array)
     KP<float> k;
     void *buf[2];
+    int *status;               // the lattice's device status word
     unsigned long long step0;  // the lattice's step count when the batch was made
     int parity0;               // its current buffer then
     int nwin2, seg_rows, pad;
@@ -1121,6 +1123,74 @@ __global__ void __maxnreg__(LB_STEP2_MAXREG) k_batch(const BatchDesc *__restrict
         RowDirect<S> rs{src, &k, A <= Amax ? A : Amax, hcol, (s > 0 || k.xper) ? s - 1 : s, k.nz, 0,
                         lane == 0 || lane == 31};
         march2<S>(k, src, dst, w * 64, s, e, salt_of(bd->step0 + t), rs);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int tk = atomicAdd(&ctl->ticket, 1u);
+        if (tk == gridDim.x - 1) {
+            ctl->ticket = 0;
+            ctl->counter = t + 1;
+            __threadfence();
+        }
+    }
+}
+
+// The batched step with the rows read in place from the TMA ring (march3):
+// one warp per work item, tensor maps from the lattice's descriptor.  The
+// step counter is read by every block before the last block advances it.
+template <typename S>
+__global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restrict__ d, const int *__restrict__ prefix,
+                                                      int n, int total, BatchCtl *ctl)
+{
+    constexpr int R = kRingStages<S>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ KP<float> skp[8];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const unsigned long long t = *(volatile unsigned long long *)&ctl->counter;
+    const int item = blockIdx.x * wpb + wib;
+    if (item < total) {
+        int lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (prefix[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const BatchDesc *bd = d + lo;
+        {
+            const uint32_t *s = reinterpret_cast<const uint32_t *>(&bd->k);
+            uint32_t *o = reinterpret_cast<uint32_t *>(&skp[wib]);
+            for (int w = lane; w < (int)(sizeof(KP<float>) / 4); w += 32) o[w] = s[w];
+        }
+        __syncwarp();
+        const KP<float> &k = skp[wib];
+        const int local = item - prefix[lo];
+        const int nw2 = bd->nwin2;
+        const int w = local % nw2, sg = local / nw2;
+        const int cur = (bd->parity0 + (int)(t & 1ULL)) & 1;
+        const int seg = bd->seg_rows;
+        const int s = sg * seg, e = min(k.nz, s + seg);
+        const bool has_m = s > 0 || k.xper, has_last = e < k.nz || k.xper;
+        const int per_warp = R * TmaGeom<S>::stage_bytes + 128;
+        unsigned char *ring = smem + per_warp * wib;
+        const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(bd->map[cur]);
+        if (lane == 0)
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((unsigned long long)map)
+                         : "memory");
+        RowRing<S, R> rs;
+        rs.map = map;
+        rs.ring = ring;
+        rs.ring_s = smem_u32(ring);
+        rs.bar_s = smem_u32(ring + R * TmaGeom<S>::stage_bytes);
+        rs.first = has_m ? s - 1 : s;
+        rs.nrows = (e - s) + (has_m ? 1 : 0) + (has_last ? 1 : 0);
+        rs.nz = k.nz;
+        rs.x0 = w * 64 - TmaGeom<S>::off;
+        rs.lane = lane;
+        rs.status = bd->status;
+        rs.start();
+        march3<S, R>(k, (const S *)bd->buf[cur], (S *)bd->buf[cur ^ 1], w * 64, s, e, salt_of(bd->step0 + t), rs);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1347,19 +1417,40 @@ int batch_items(const HostParams &h, int seg_rows)
     return nwindows2(h.nr) * ((h.nz + seg_rows - 1) / seg_rows);
 }
 
-void batch_fill_desc(const HostParams &h, void *buf0, void *buf1, unsigned long long step0, int parity0,
-                     int seg_rows, void *out)
+cudaError_t batch_fill_desc(const HostParams &h, void *buf0, void *buf1, unsigned long long step0, int parity0,
+                            int seg_rows, int *status, void *out)
 {
     BatchDesc d;
     std::memset(&d, 0, sizeof(d));
+    cudaError_t e = make_tensor_map(h, buf0, d.map[0]);
+    if (e == cudaSuccess) e = make_tensor_map(h, buf1, d.map[1]);
+    if (e != cudaSuccess) return e;
     d.k = make_kp<float>(h);
     d.buf[0] = buf0;
     d.buf[1] = buf1;
+    d.status = status;
     d.step0 = step0;
     d.parity0 = parity0;
     d.nwin2 = nwindows2(h.nr);
     d.seg_rows = seg_rows;
     std::memcpy(out, &d, sizeof(d));
+    return cudaSuccess;
+}
+
+cudaError_t batch_prepare(int storage)
+{
+    switch (storage) {
+        case ST_FP32:
+            return cudaFuncSetAttribute(k_batch3<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)ring_smem_bytes<float>(8));
+        case ST_FP16:
+            return cudaFuncSetAttribute(k_batch3<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)ring_smem_bytes<__half>(8));
+        case ST_BF16:
+            return cudaFuncSetAttribute(k_batch3<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)ring_smem_bytes<__nv_bfloat16>(8));
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 int batch_grid(int storage, int wpb)
@@ -1376,12 +1467,30 @@ int batch_grid(int storage, int wpb)
     return sms * (per > 0 ? per : 1);
 }
 
-cudaError_t launch_batch(int storage, const void *desc, const int *prefix, int n, int total, void *ctl, int wpb,
-                         int blocks, cudaStream_t s)
+cudaError_t launch_batch(int storage, int row_fetch, const void *desc, const int *prefix, int n, int total,
+                         void *ctl, int wpb, int blocks, cudaStream_t s)
 {
     const int need = (total + wpb - 1) / wpb;
+    if (need < 1) return cudaSuccess;
+    if (row_fetch == 3) {
+        const BatchDesc *dd = (const BatchDesc *)desc;
+        BatchCtl *cc = (BatchCtl *)ctl;
+        switch (storage) {
+            case ST_FP32:
+                k_batch3<float><<<need, 32 * wpb, ring_smem_bytes<float>(wpb), s>>>(dd, prefix, n, total, cc);
+                break;
+            case ST_FP16:
+                k_batch3<__half><<<need, 32 * wpb, ring_smem_bytes<__half>(wpb), s>>>(dd, prefix, n, total, cc);
+                break;
+            case ST_BF16:
+                k_batch3<__nv_bfloat16>
+                    <<<need, 32 * wpb, ring_smem_bytes<__nv_bfloat16>(wpb), s>>>(dd, prefix, n, total, cc);
+                break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     const int grid = blocks < need ? blocks : need;
-    if (grid < 1) return cudaSuccess;
     switch (storage) {
         case ST_FP32:
             k_batch<float><<<grid, 32 * wpb, 0, s>>>((const BatchDesc *)desc, prefix, n, total, (BatchCtl *)ctl);

@@ -49,10 +49,12 @@ def test_batch_equals_individual_runs(storage, row_fetch):
         s = Solver(c.params, storage=storage, stream=stream)
         s.init_fields(c.fields)
         mixed.append(s)
-    b = Batch(mixed, stream=stream, graph_steps=8)
+    b = Batch(mixed, stream=stream, graph_steps=8)  # TMA ring read in place, one warp per item
     b.step(5)
-    b.set_launch(seg_rows=5, warps_per_block=4, graph_steps=4)
-    b.step(32)  # 8 graph replays of 4 launches
+    b.set_launch(seg_rows=5, warps_per_block=4, graph_steps=4, row_fetch=1)  # plain loads, persistent grid
+    b.step(16)  # 4 graph replays of 4 launches
+    b.set_launch(seg_rows=3, warps_per_block=2, graph_steps=4, row_fetch=3)
+    b.step(16)
     torch.cuda.synchronize()
     for c, a, s in zip(cases, alone, mixed):
         assert s.step_count == 37
