@@ -531,6 +531,8 @@ struct lb_batch {
     unsigned long long counter;
     cudaGraphExec_t gexec;
     bool graph_valid;
+    cudaEvent_t ev;                      // orders the batch stream against the lattices' streams
+    std::vector<cudaStream_t> streams;   // the lattices' distinct streams other than the batch's
     std::vector<unsigned char> hdesc;
     std::vector<int> hprefix;
 };
@@ -618,15 +620,24 @@ lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_buf, size_t 
     b->counter = 0;
     b->graph_valid = false;
     b->blocks = lbk::batch_grid(storage, b->wpb);
-    cudaError_t e = lbk::batch_prepare(storage);
+    b->ev = nullptr;
+    for (int m = 0; m < n; ++m) {
+        cudaStream_t s = ctxs[m]->stream;
+        bool seen = s == b->stream;
+        for (cudaStream_t t : b->streams) seen = seen || t == s;
+        if (!seen) b->streams.push_back(s);
+    }
+    cudaError_t e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = lbk::batch_prepare(storage);
+    if (e == cudaSuccess) e = batch_streams_wait(b, true);  // the lattices' pending work precedes the batch
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctl, 0, lbk::batch_ctl_bytes(), b->stream);
     if (e != cudaSuccess) {
-        delete b;
+        lb_batch_destroy(b);
         return cuda_fail(nullptr, e, "batch reset");
     }
     lb_status st = batch_upload(b);
     if (st != LB_OK) {
-        delete b;
+        lb_batch_destroy(b);
         return st;
     }
     *out = b;
@@ -650,9 +661,27 @@ lb_status lb_batch_set_launch(lb_batch *b, int32_t seg_rows, int32_t warps_per_b
     return batch_upload(b);
 }
 
+// Work queued on the lattices' own streams (initialisation, state uploads,
+// diagnostics) and the batch's launches stay ordered both ways.
+static cudaError_t batch_streams_wait(lb_batch *b, bool batch_waits)
+{
+    cudaError_t e = cudaSuccess;
+    for (cudaStream_t s : b->streams) {
+        cudaStream_t from = batch_waits ? s : b->stream, to = batch_waits ? b->stream : s;
+        e = cudaEventRecord(b->ev, from);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(to, b->ev, 0);
+        if (e != cudaSuccess) break;
+    }
+    return e;
+}
+
 lb_status lb_batch_step(lb_batch *b, int32_t nsteps)
 {
     if (!b || nsteps < 0) return fail(nullptr, LB_ERR_ARG, "batch is NULL or nsteps < 0");
+    {
+        cudaError_t e = batch_streams_wait(b, true);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch stream order");
+    }
     int32_t left = nsteps;
     const bool use_graph = b->graph_steps > 1 && b->stream != nullptr && left >= b->graph_steps;
     if (use_graph && !b->graph_valid) {
@@ -686,12 +715,15 @@ lb_status lb_batch_step(lb_batch *b, int32_t nsteps)
         c->step = (int64_t)(b->step0[m] + b->counter);
         c->cur = (int)((b->parity0[m] + b->counter) & 1ULL);
     }
+    cudaError_t e = batch_streams_wait(b, false);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch stream order");
     return LB_OK;
 }
 
 lb_status lb_batch_destroy(lb_batch *b)
 {
     if (b && b->graph_valid) cudaGraphExecDestroy(b->gexec);
+    if (b && b->ev) cudaEventDestroy(b->ev);
     delete b;
     return LB_OK;
 }
