@@ -537,6 +537,20 @@ struct lb_batch {
     std::vector<int> hprefix;
 };
 
+// Work queued on the lattices' own streams (initialisation, state uploads,
+// diagnostics) and the batch's launches stay ordered both ways.
+static cudaError_t batch_streams_wait(lb_batch *b, bool batch_waits)
+{
+    cudaError_t e = cudaSuccess;
+    for (cudaStream_t s : b->streams) {
+        cudaStream_t from = batch_waits ? s : b->stream, to = batch_waits ? b->stream : s;
+        e = cudaEventRecord(b->ev, from);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(to, b->ev, 0);
+        if (e != cudaSuccess) break;
+    }
+    return e;
+}
+
 static size_t batch_layout(int32_t n, size_t *desc_off, size_t *prefix_off, size_t *ctl_off)
 {
     const size_t d = align256((size_t)n * lbk::batch_desc_bytes());
@@ -659,20 +673,6 @@ lb_status lb_batch_set_launch(lb_batch *b, int32_t seg_rows, int32_t warps_per_b
     }
     b->graph_steps = graph_steps;
     return batch_upload(b);
-}
-
-// Work queued on the lattices' own streams (initialisation, state uploads,
-// diagnostics) and the batch's launches stay ordered both ways.
-static cudaError_t batch_streams_wait(lb_batch *b, bool batch_waits)
-{
-    cudaError_t e = cudaSuccess;
-    for (cudaStream_t s : b->streams) {
-        cudaStream_t from = batch_waits ? s : b->stream, to = batch_waits ? b->stream : s;
-        e = cudaEventRecord(b->ev, from);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(to, b->ev, 0);
-        if (e != cudaSuccess) break;
-    }
-    return e;
 }
 
 lb_status lb_batch_step(lb_batch *b, int32_t nsteps)
