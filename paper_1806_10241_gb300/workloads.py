@@ -164,6 +164,78 @@ def swirling_cylinder(nr: int = 1024, nz: int = 2048, Re: float = 1000.0, Ra: fl
     return Case("swirling_cylinder", params, rest_fields(nz, nr, T))
 
 
+def rayleigh_benard_cylinder(nr: int = 100, nz: int = 100, Ra: float = 5e3, Pr: float = 0.7,
+                             tau: float = 0.85, T_init: float = 0.0, amp: float = 0.0, seed: int = 0,
+                             T_hot: float = 1.0, T_cold: float = 0.0) -> Case:
+    """Rayleigh-Benard convection in a vertical cylinder (Sec. 3.3, Table 2).
+
+    Radius R = nr, height H = nz (aspect ratio H/R = nz / nr), axis of
+    symmetry at r = 0, heated bottom T_hot, cooled top T_cold, adiabatic
+    side wall, no-slip walls.  The shear relaxation time tau fixes
+    nu = (tau - 1/2) / 3; Ra = g beta dT H^3 / (nu alpha).  The fluid starts
+    at rest at T = T_init (T_cold gives the up-flow pattern of Fig. 5).
+    """
+    H = float(nz)
+    nu = (tau - 0.5) / 3.0
+    alpha = nu / Pr
+    dT = T_hot - T_cold
+    g_beta = Ra * nu * alpha / (dT * H ** 3)
+    sides = [_side(heat=SC_DIRICHLET, T_w=T_hot), _side(heat=SC_DIRICHLET, T_w=T_cold),
+             _axis(), _side(heat=SC_NEUMANN)]
+    params = {"nr": nr, "nz": nz, "r0": 0.0, "nu": nu, "alpha": alpha, "g_beta": g_beta,
+              "T0": 0.5 * (T_hot + T_cold), "rho0": 1.0, "omega3": 1.0, "omega_hi": 1.0, "sides": sides}
+    T = perturbed_T(nz, nr, T_init, amp, seed)
+    return Case("rayleigh_benard_cylinder", params, rest_fields(nz, nr, T))
+
+
+def buoyancy_velocity(params: dict) -> float:
+    """sqrt(g beta H dT) of a heated cylinder or annulus (dT from the
+    Dirichlet walls), the velocity scale of Table 2."""
+    tw = [s["T_w"] for s in params["sides"] if s["heat"] == SC_DIRICHLET]
+    return math.sqrt(params["g_beta"] * params["nz"] * (max(tw) - min(tw)))
+
+
+def mixed_convection_annulus(D: int = 40, eta: float = 10.0, ratio: float = 2.0, Re: float = 100.0,
+                             sigma: float = 0.0, Pr: float = 0.7, u_inner: float = 0.05,
+                             amp: float = 1e-4, seed: int = 0, T_hot: float = 1.0,
+                             T_cold: float = 0.0) -> Case:
+    """Mixed convection in a slender annulus with a rotating inner cylinder
+    (Sec. 3.5, Table 3).
+
+    Gap D = R_o - R_i = nr, height H = eta D = nz, R_o / R_i = ratio, inner
+    wall speed u_inner = Omega_i R_i, Re = Omega_i R_i D / nu,
+    Gr = g beta dT D^3 / nu^2 = sigma Re^2.  Hot inner wall, cold outer wall,
+    adiabatic ends, fixed outer cylinder and ends.  T starts at the
+    conduction profile plus a seeded perturbation that seeds the Taylor cells.
+    """
+    nr, nz = int(D), int(round(eta * D))
+    L = float(nr)
+    r0 = L / (ratio - 1.0)
+    nu = u_inner * L / Re
+    alpha = nu / Pr
+    dT = T_hot - T_cold
+    g_beta = sigma * Re * Re * nu * nu / (dT * L ** 3)
+    sides = [_side(heat=SC_NEUMANN), _side(heat=SC_NEUMANN),
+             _side(heat=SC_DIRICHLET, T_w=T_hot, omega=u_inner / r0),
+             _side(heat=SC_DIRICHLET, T_w=T_cold)]
+    params = {"nr": nr, "nz": nz, "r0": r0, "nu": nu, "alpha": alpha, "g_beta": g_beta,
+              "T0": 0.5 * (T_hot + T_cold), "rho0": 1.0, "omega3": 1.0, "omega_hi": 1.0, "sides": sides}
+    y = radii(nr, r0)
+    R_o = r0 + L
+    base = T_cold + dT * np.log(y / R_o) / math.log(r0 / R_o)
+    T = perturbed_T(nz, nr, base[None, :], amp, seed)
+    return Case("mixed_convection_annulus", params, rest_fields(nz, nr, T))
+
+
+def k_eq_inner(params: dict, nu_inner: float) -> float:
+    """Mean equivalent conductivity at the inner cylinder (Sec. 3.5):
+    ln(R_o / R_i) / (H dT) * integral over z of (-r dT/dr) at R_i, i.e. the
+    inner-wall Nusselt number -R_i/(H dT) sum dT/dr times ln(R_o / R_i);
+    1 for pure conduction."""
+    r0 = params["r0"]
+    return nu_inner * math.log((r0 + params["nr"]) / r0)
+
+
 def taylor_couette(R_o: int = 50, beta: float = 0.5, kappa: float = 0.1, tau: float = 0.6,
                    Re: float = 5.0, nz: int = 3) -> Case:
     """Circular Couette flow between rotating cylinders (Sec. 3.1).

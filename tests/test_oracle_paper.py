@@ -4,6 +4,10 @@ Table 1 (Sec. 3.2) gives the mean Nusselt number of natural convection in a
 vertical annulus computed on a 200 x 200 grid.  The oracle runs the same
 problem on much coarser grids, so the pin is loose (about 1 %); the values
 converge towards the table as the grid is refined.
+
+Table 2 (Sec. 3.3) gives the maximum velocity of Rayleigh-Benard convection
+in a cylinder on the paper's own 100 x 100 grid and relaxation time, so the
+oracle runs exactly that problem and must reproduce the printed 3 digits.
 """
 import os
 
@@ -51,3 +55,34 @@ def test_annulus_nusselt_converges_towards_table1():
         case = W.annulus_convection(nr=L, nz=2 * L, ratio=2.0, Ra=1e3, Pr=0.7, amp=0.0)
         errs.append(abs(run_to_steady_nu(case)["nu_avg"] - nu_paper))
     assert errs[1] < errs[0]
+
+
+GOLDEN_RB = os.path.join(os.path.dirname(__file__), "golden", "table2_rb_umax.txt")
+
+
+def table2():
+    rows = [l.split() for l in open(GOLDEN_RB) if l.strip() and not l.startswith("#")]
+    return {a: float(b) for a, b in rows}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("T_init", [0.0, 1.0])
+def test_rayleigh_benard_cylinder_max_velocity_matches_table2(T_init):
+    """Sec. 3.3, Table 2: the steady Rayleigh-Benard cell in a cylinder
+    (Ra = 5e3, Pr = 0.7, H/R = 1, 100 x 100, tau = 0.85).  The two steady
+    patterns are told apart by the sign of the axial velocity on the axis
+    at mid-height; starting from T = T_cold gives the cell with down-flow on
+    the axis, from T = T_hot the one with up-flow.  The printed u_max of the
+    pattern (3 digits) is matched to 0.5 %."""
+    case = W.rayleigh_benard_cylinder(T_init=T_init, amp=1e-3, seed=1)
+    o = oracle.Oracle(case.params)
+    o.init_fields(case.fields)
+    o.step(60000)
+    d = o.diag()
+    f = o.fields()
+    pattern = "up-flow" if f[1][case.nz // 2, 0] > 0 else "down-flow"
+    assert pattern == ("up-flow" if T_init > 0.5 else "down-flow")
+    ratio = d["u_max"] / W.buoyancy_velocity(case.params)
+    assert ratio == pytest.approx(table2()[pattern], rel=5e-3), (pattern, ratio)
+    # a steady single cell: the radial velocity vanishes on the axis
+    assert np.max(np.abs(f[2][:, 0])) < 0.05 * d["u_max"]
