@@ -410,8 +410,8 @@ struct DiagAcc {
 
 template <typename S, typename C, int MODE>
 __device__ __forceinline__ void march(const KP<C> &k, const S *__restrict__ src, S *__restrict__ dst,
-                                      double *__restrict__ fout, int fout_row0, int c, int row_s,
-                                      int row_e, DiagAcc *acc)
+                                      double *__restrict__ fout, int fout_row0, int fout_rows, int c,
+                                      int row_s, int row_e, DiagAcc *acc)
 {
     const int lane = threadIdx.x & 31;
     const int nr = k.nr, nz = k.nz;
@@ -596,7 +596,7 @@ __device__ __forceinline__ void march(const KP<C> &k, const S *__restrict__ src,
             }
         } else if (MODE == MODE_FIELDS) {
             if (out_lane) {
-                const long long n = (long long)(row_e - fout_row0) * nr;
+                const long long n = (long long)fout_rows * nr;  // plane stride of the output chunk
                 double *p = fout + (long long)(i - fout_row0) * nr + c;
                 p[0] = (double)o.rho;
                 p[n] = (double)o.ux;
@@ -663,7 +663,7 @@ __device__ __forceinline__ void step_body(const KP<C> &k, const S *__restrict__ 
     const int c = warp * OUT_COLS - 1 + (threadIdx.x & 31);
     const int s = blockIdx.y * seg_rows;
     const int e = min(k.nz, s + seg_rows);
-    march<S, C, MODE_STEP>(k, src, dst, nullptr, 0, c, s, e, nullptr);
+    march<S, C, MODE_STEP>(k, src, dst, nullptr, 0, 0, c, s, e, nullptr);
 }
 
 // FP32-compute step (FP32 / BF16 / FP16 storage): register cap for 24
@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(256) k_fields(KP<C> k, const S *__restrict__ s
     if (warp >= nwin) return;
     const int c = warp * OUT_COLS - 1 + (threadIdx.x & 31);
     const int s = row0 + blockIdx.y * kFieldRows, e = min(row1, s + kFieldRows);
-    march<S, C, MODE_FIELDS>(k, src, nullptr, out, row0, c, s, e, nullptr);
+    march<S, C, MODE_FIELDS>(k, src, nullptr, out, row0, row1 - row0, c, s, e, nullptr);
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -824,7 +824,7 @@ __global__ void __launch_bounds__(128) k_diag(KP<C> k, const S *__restrict__ src
     if (warp < nwin) {
         const int c = warp * OUT_COLS - 1 + lane;
         const int s = blockIdx.y * seg_rows, e = min(k.nz, s + seg_rows);
-        march<S, C, MODE_DIAG>(k, src, nullptr, tfield, 0, c, s, e, &a);
+        march<S, C, MODE_DIAG>(k, src, nullptr, tfield, 0, 0, c, s, e, &a);
     }
     double vals[NSUM] = {a.mass_dev, a.mass_r_dev, a.tsum, a.umax, 0, 0, 0, 0, a.bad, 0, 0, 0};
 #pragma unroll
@@ -892,7 +892,7 @@ __global__ void __launch_bounds__(128) k_diag_strip(KP<C> k, const S *__restrict
     if (warp < nwin) {
         const int c = warp * OUT_COLS - 1 + lane;
         const int s = blockIdx.y * seg_rows, e = min(k.nz, s + seg_rows);
-        march<S, C, MODE_DIAG_STRIP>(k, src, nullptr, strips, 0, c, s, e, &a);
+        march<S, C, MODE_DIAG_STRIP>(k, src, nullptr, strips, 0, 0, c, s, e, &a);
     }
     double vals[NSUM] = {a.mass_dev, a.mass_r_dev, a.tsum, a.umax, 0, 0, 0, 0, a.bad, 0, 0, 0};
 #pragma unroll
