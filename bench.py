@@ -398,8 +398,9 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * dt / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(nr, nz, "fp64") + f" -- slab {nr}x{rows} per step",
-                       "nr": nr, "nz": nz, "slab_rows": rows, "parallelism": "replicas"},
+            "config": {"workload": workload_desc(nr, nz, args.storage), "nr": nr, "nz": nz,
+                       "storage": args.storage, "parallelism": "replicas",
+                       "oracle": f"FP64, a {nr}x{rows} slab of the lattice per step (same per-node work)"},
             "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
                              "sample": f"{args.steps} steps of a {nr}x{rows} slab after {args.warmup} "
                                        f"warm-up steps, {threads} OpenMP threads"},

@@ -1,0 +1,48 @@
+"""The GPU path against numbers printed in the paper.
+
+Table 2 (Sec. 3.3): u_max / sqrt(g beta H dT) of the steady Rayleigh-Benard
+cell in a cylinder, Ra = 5e3, Pr = 0.7, H/R = 1, on the paper's 100 x 100
+grid with tau = 0.85.  The cell with up-flow on the axis comes from
+T = T_hot, the one with down-flow from T = T_cold (the same runs pin the
+oracle in tests/test_oracle_paper.py).  FP32 and FP64 storage.
+"""
+import os
+
+import pytest
+
+from paper_1806_10241_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _table(name, key=str):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, name)) if l.strip() and not l.startswith("#")]
+    return {key(a): float(b) for a, b in rows}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_10241_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp64"])
+@pytest.mark.parametrize("T_init", [0.0, 1.0])
+def test_rayleigh_benard_cylinder_max_velocity_matches_table2(T_init, storage):
+    from paper_1806_10241_gb300.solver import Solver
+    case = W.rayleigh_benard_cylinder(T_init=T_init, amp=1e-3, seed=1)
+    s = Solver(case.params, storage=storage)
+    s.init_fields(case.fields)
+    s.step(60000)
+    d = s.diag()
+    assert d["status"] == 0
+    f = s.fields()
+    pattern = "up-flow" if f[1][case.nz // 2, 0] > 0 else "down-flow"
+    assert pattern == ("up-flow" if T_init > 0.5 else "down-flow")
+    ratio = d["u_max"] / W.buoyancy_velocity(case.params)
+    assert ratio == pytest.approx(_table("table2_rb_umax.txt")[pattern], rel=5e-3), (pattern, ratio)
