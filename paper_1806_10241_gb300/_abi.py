@@ -73,6 +73,7 @@ PROTOTYPES = {
     "lb_batch_create": (_st, [C.POINTER(_vp), C.c_int32, _vp, C.c_size_t, _vp, C.POINTER(_vp)]),
     "lb_batch_set_launch": (_st, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "lb_batch_step": (_st, [_vp, C.c_int32]),
+    "lb_batch_diagnostics": (_st, [_vp, _vp]),
     "lb_batch_destroy": (_st, [_vp]),
     "lb_destroy": (_st, [_vp]),
     "lb_last_error": (C.c_char_p, [_vp]),

@@ -11,7 +11,7 @@ import ctypes as C
 import torch
 
 from . import _abi
-from .solver import Solver
+from .solver import Solver, diag_dict
 
 
 class Batch:
@@ -41,6 +41,12 @@ class Batch:
 
     def step(self, n: int = 1) -> None:
         _abi.check(self.L.lb_batch_step(self.h, int(n)))
+
+    def diag(self) -> list:
+        """Diagnostics of every lattice (one download for the whole batch)."""
+        out = (_abi.lb_diag * len(self.solvers))()
+        _abi.check(self.L.lb_batch_diagnostics(self.h, C.cast(out, C.c_void_p)))
+        return [diag_dict(d) for d in out]
 
     def close(self) -> None:
         if getattr(self, "h", None):

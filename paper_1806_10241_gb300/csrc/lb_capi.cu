@@ -340,21 +340,10 @@ lb_status lb_get_fields(lb_ctx *ctx, double *host_fields)
     return LB_OK;
 }
 
-lb_status lb_diagnostics(lb_ctx *ctx, lb_diag *out)
+// lb_diag from the NSUM device sums of the diagnostics and the status word
+static void fill_diag(const lb_ctx *ctx, const double *res, int kstatus, lb_diag *out)
 {
-    lb_status st = need_params(ctx);
-    if (st != LB_OK) return st;
-    if (!out) return fail(ctx, LB_ERR_ARG, "out is NULL");
     const HostParams &h = ctx->hp;
-    double res[lbk::NSUM];
-    int kstatus = 0;
-    cudaError_t e = lbk::launch_diag(h, diag_launch(ctx), ctx->dist[ctx->cur], ctx->partial,
-                                     (double *)ctx->dist[1 - ctx->cur], ctx->result, ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "diagnostics kernel");
-    e = cudaMemcpyAsync(&kstatus, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(res, ctx->result, sizeof(res), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "diagnostics download");
     std::memset(out, 0, sizeof(*out));
     const double N = (double)h.nr * h.nz;
     const double sum_y = (double)h.nz * (h.nr * h.r0 + 0.5 * (double)h.nr * h.nr);
@@ -383,6 +372,24 @@ lb_status lb_diagnostics(lb_ctx *ctx, lb_diag *out)
     out->step = ctx->step;
     const bool bad = res[8] > 0.0 || !std::isfinite(res[0]) || !std::isfinite(res[2]);
     out->status = kstatus ? kstatus : (bad ? LB_ERR_DIVERGED : LB_OK);
+}
+
+lb_status lb_diagnostics(lb_ctx *ctx, lb_diag *out)
+{
+    lb_status st = need_params(ctx);
+    if (st != LB_OK) return st;
+    if (!out) return fail(ctx, LB_ERR_ARG, "out is NULL");
+    const HostParams &h = ctx->hp;
+    double res[lbk::NSUM];
+    int kstatus = 0;
+    cudaError_t e = lbk::launch_diag(h, diag_launch(ctx), ctx->dist[ctx->cur], ctx->partial,
+                                     (double *)ctx->dist[1 - ctx->cur], ctx->result, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "diagnostics kernel");
+    e = cudaMemcpyAsync(&kstatus, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(res, ctx->result, sizeof(res), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "diagnostics download");
+    fill_diag(ctx, res, kstatus, out);
     return LB_OK;
 }
 
@@ -526,6 +533,8 @@ struct lb_batch {
     void *d_desc;
     int *d_prefix;
     void *d_ctl;
+    char *d_diag;
+    std::vector<char> hdiag;
     cudaStream_t stream;
     int seg_rows, wpb, blocks, total, graph_steps, row_fetch;
     unsigned long long counter;
@@ -551,14 +560,18 @@ static cudaError_t batch_streams_wait(lb_batch *b, bool batch_waits)
     return e;
 }
 
-static size_t batch_layout(int32_t n, size_t *desc_off, size_t *prefix_off, size_t *ctl_off)
+constexpr size_t kDiagSlot = 256;  // per lattice: its NSUM sums and status word, gathered on the device
+
+static size_t batch_layout(int32_t n, size_t *desc_off, size_t *prefix_off, size_t *ctl_off, size_t *diag_off)
 {
     const size_t d = align256((size_t)n * lbk::batch_desc_bytes());
     const size_t p = align256((size_t)(n + 1) * sizeof(int));
+    const size_t t = align256(lbk::batch_ctl_bytes());
     *desc_off = 0;
     *prefix_off = d;
     *ctl_off = d + p;
-    return d + p + align256(lbk::batch_ctl_bytes());
+    *diag_off = d + p + t;
+    return d + p + t + (size_t)n * kDiagSlot;
 }
 
 static lb_status batch_upload(lb_batch *b)
@@ -591,8 +604,8 @@ static lb_status batch_upload(lb_batch *b)
 lb_status lb_batch_required_bytes(int32_t n, size_t *bytes)
 {
     if (n < 1 || !bytes) return fail(nullptr, LB_ERR_ARG, "n >= 1 and bytes required");
-    size_t a, b, c;
-    *bytes = batch_layout(n, &a, &b, &c);
+    size_t a, b, c, d;
+    *bytes = batch_layout(n, &a, &b, &c, &d);
     return LB_OK;
 }
 
@@ -601,8 +614,8 @@ lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_buf, size_t 
 {
     if (!out || !ctxs || n < 1 || !dev_buf) return fail(nullptr, LB_ERR_ARG, "NULL argument or n < 1");
     *out = nullptr;
-    size_t doff, poff, coff;
-    const size_t need = batch_layout(n, &doff, &poff, &coff);
+    size_t doff, poff, coff, goff;
+    const size_t need = batch_layout(n, &doff, &poff, &coff, &goff);
     if (bytes < need) return fail(nullptr, LB_ERR_NOMEM, "batch buffer holds %zu bytes, %zu needed", bytes, need);
     if (((uintptr_t)dev_buf & 255) != 0) return fail(nullptr, LB_ERR_ARG, "dev_buf must be 256-byte aligned");
     const int storage = ctxs[0] ? ctxs[0]->hp.storage : -1;
@@ -626,6 +639,8 @@ lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_buf, size_t 
     b->d_desc = b->buf + doff;
     b->d_prefix = (int *)(b->buf + poff);
     b->d_ctl = b->buf + coff;
+    b->d_diag = b->buf + goff;
+    b->hdiag.assign((size_t)n * kDiagSlot, 0);
     b->stream = (cudaStream_t)cuda_stream;
     b->seg_rows = 4;
     b->wpb = 1;
@@ -717,6 +732,33 @@ lb_status lb_batch_step(lb_batch *b, int32_t nsteps)
     }
     cudaError_t e = batch_streams_wait(b, false);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch stream order");
+    return LB_OK;
+}
+
+lb_status lb_batch_diagnostics(lb_batch *b, lb_diag *out)
+{
+    if (!b || !out) return fail(nullptr, LB_ERR_ARG, "batch or out is NULL");
+    cudaError_t e = batch_streams_wait(b, true);
+    const size_t res_bytes = 128 + sizeof(int);  // NSUM sums, padding, status word
+    for (size_t m = 0; e == cudaSuccess && m < b->ctxs.size(); ++m) {
+        lb_ctx *c = b->ctxs[m];
+        e = lbk::launch_diag(c->hp, diag_launch(c), c->dist[c->cur], c->partial, (double *)c->dist[1 - c->cur],
+                             c->result, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_diag + m * kDiagSlot, c->result, res_bytes, cudaMemcpyDeviceToDevice,
+                                b->stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->hdiag.data(), b->d_diag, b->hdiag.size(), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = batch_streams_wait(b, false);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch diagnostics");
+    for (size_t m = 0; m < b->ctxs.size(); ++m) {
+        const char *slot = b->hdiag.data() + m * kDiagSlot;
+        int kstatus;
+        std::memcpy(&kstatus, slot + 128, sizeof(int));
+        fill_diag(b->ctxs[m], reinterpret_cast<const double *>(slot), kstatus, &out[m]);
+    }
     return LB_OK;
 }
 

@@ -742,11 +742,12 @@ __global__ void __maxnreg__(LB_STEP2_MAXREG)
 }
 
 // The step with the rows resident in the TMA ring (march3): no row carried
-// in registers.  kRingStages<S> stages of one row each per warp.
+// in registers.  kRingStages<S> stages of one row each per warp: rows i-1,
+// i, i+1 of the step and one more in flight.
 #ifndef LB_STEP3_MAXREG
 #define LB_STEP3_MAXREG 168
 #endif
-template <typename S> constexpr int kRingStages = sizeof(S) == 4 ? 3 : 4;
+template <typename S> constexpr int kRingStages = 4;
 
 template <typename S>
 size_t ring_smem_bytes(int wpb)

@@ -127,9 +127,11 @@ class Server:
         rec.admitted = now
         return _Active(req, s, rec, required_bytes(req.case.params, self.storage))
 
-    def _check(self, a: _Active) -> bool:
-        """Diagnostics of an active lattice; True when it is finished."""
-        d = a.solver.diag()
+    def _check(self, a: _Active, d: dict | None = None) -> bool:
+        """Diagnostics of an active lattice (given, or computed here); True
+        when it is finished."""
+        if d is None:
+            d = a.solver.diag()
         a.rec.steps = d["step"]
         a.rec.nu = d["nu_avg"]
         a.history.append((d["step"], d["nu_avg"]))
@@ -198,12 +200,14 @@ class Server:
             if on_round is not None:
                 on_round(self, clock() - t0)
             finished = []
-            for a in active:
+            due = [a.solver.step_count % self.check_every == 0 for a in active]
+            diags = batch.diag() if any(due) else None  # every lattice's diagnostics in one download
+            for a, is_due, d in zip(active, due, diags or [None] * len(active)):
                 if a.rec.rid in self._cancelled:
                     a.rec.steps = a.solver.step_count
                     a.rec.status = "cancelled"
                     finished.append(a)
-                elif a.solver.step_count % self.check_every == 0 and self._check(a):
+                elif is_due and self._check(a, d):
                     finished.append(a)
             if finished:
                 now = clock() - t0

@@ -26,6 +26,13 @@ def required_bytes(params: dict, storage: str = "fp32") -> int:
     return int(n.value)
 
 
+def diag_dict(d) -> dict:
+    """lb_diag as a dict."""
+    return {"nu_side": list(d.nu_side), "nu_i": d.nu_i, "nu_o": d.nu_o, "nu_avg": d.nu_avg,
+            "mass": d.mass, "mass_r": d.mass_r, "T_sum": d.T_sum, "u_max": d.u_max,
+            "step": int(d.step), "status": int(d.status)}
+
+
 class Solver:
     """A lattice whose distributions live on `device`.
 
@@ -109,9 +116,7 @@ class Solver:
     def diag(self) -> dict:
         d = _abi.lb_diag()
         self._check(self.L.lb_diagnostics(self.ctx, C.byref(d)))
-        return {"nu_side": list(d.nu_side), "nu_i": d.nu_i, "nu_o": d.nu_o, "nu_avg": d.nu_avg,
-                "mass": d.mass, "mass_r": d.mass_r, "T_sum": d.T_sum, "u_max": d.u_max,
-                "step": int(d.step), "status": int(d.status)}
+        return diag_dict(d)
 
     def get_dist(self) -> np.ndarray:
         a = np.empty((19, self.nz, self.nr), np.float64)

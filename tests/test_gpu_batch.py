@@ -85,3 +85,21 @@ def test_batch_matches_oracle_fp32():
                 assert np.linalg.norm(got[q] - want[q]) / n < 1e-5, (c.name, q)
         d = s.diag()
         assert d["status"] == 0 and d["step"] == 300
+
+
+def test_batch_diagnostics_equal_per_lattice_diagnostics():
+    from paper_1806_10241_gb300.batch import Batch
+    from paper_1806_10241_gb300.solver import Solver
+    stream = torch.cuda.Stream()
+    sols = []
+    for c in _cases():
+        s = Solver(c.params, storage="fp16", stream=stream)
+        s.init_fields(c.fields)
+        sols.append(s)
+    b = Batch(sols, stream=stream, graph_steps=5)
+    b.step(25)
+    together = b.diag()
+    alone = [s.diag() for s in sols]
+    for t, a in zip(together, alone):
+        assert t == a
+    b.close()

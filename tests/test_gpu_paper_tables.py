@@ -1,10 +1,20 @@
-"""The GPU path against numbers printed in the paper.
+"""The GPU path against numbers printed in the paper (FP32 and FP64 paths are
+pinned to the oracle by the parity tests).
 
 Table 2 (Sec. 3.3): u_max / sqrt(g beta H dT) of the steady Rayleigh-Benard
 cell in a cylinder, Ra = 5e3, Pr = 0.7, H/R = 1, on the paper's 100 x 100
 grid with tau = 0.85.  The cell with up-flow on the axis comes from
 T = T_hot, the one with down-flow from T = T_cold (the same runs pin the
 oracle in tests/test_oracle_paper.py).  FP32 and FP64 storage.
+
+Table 3 (Sec. 3.5): the mean equivalent conductivity k_eq at the rotating
+inner cylinder of a slender annulus (Re = 100, Pr = 0.7, R_o/R_i = 2,
+H/D = 10) on the paper's 40 x 400 grid, at sigma = Gr/Re^2 = 0, 0.01, 0.05,
+run to the steady Taylor-vortex state.  The printed values (3 digits) are
+matched to 1.5 % (the two reference solutions the paper quotes differ from
+each other by up to 6 %); the Taylor cells are counted by the sign changes
+of the radial velocity along z at mid-gap: five pairs without buoyancy and
+four pairs at sigma = 0.05, as the paper describes.
 """
 import os
 
@@ -46,3 +56,22 @@ def test_rayleigh_benard_cylinder_max_velocity_matches_table2(T_init, storage):
     assert pattern == ("up-flow" if T_init > 0.5 else "down-flow")
     ratio = d["u_max"] / W.buoyancy_velocity(case.params)
     assert ratio == pytest.approx(_table("table2_rb_umax.txt")[pattern], rel=5e-3), (pattern, ratio)
+
+
+@pytest.mark.parametrize("sigma,steps,sign_changes", [(0.0, 600000, 10), (0.01, 2000000, None),
+                                                     (0.05, 600000, 8)])
+def test_mixed_convection_keq_matches_table3(sigma, steps, sign_changes):
+    import numpy as np
+    from paper_1806_10241_gb300.solver import Solver
+    case = W.mixed_convection_annulus(sigma=sigma)
+    s = Solver(case.params, storage="fp32")
+    s.init_fields(case.fields)
+    s.step(steps)
+    d = s.diag()
+    assert d["status"] == 0
+    k_eq = W.k_eq_inner(case.params, d["nu_i"])
+    assert k_eq == pytest.approx(_table("table3_keq.txt", float)[sigma], rel=1.5e-2), (sigma, k_eq)
+    if sign_changes is not None:
+        uy = s.fields()[2][:, case.nr // 2]
+        sign = np.sign(uy[np.abs(uy) > 1e-3 * np.abs(uy).max()])
+        assert int(np.sum(sign[1:] != sign[:-1])) == sign_changes
