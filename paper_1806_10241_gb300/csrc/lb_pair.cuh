@@ -4,10 +4,15 @@
 // A warp owns 64 adjacent, 64-aligned columns: lane l holds columns
 // c0 + 2l ("x" of every pair) and c0 + 2l + 1 ("y").  Rows are read and
 // written as float2 / half2 pairs, so each warp touches whole 128-byte lines
-// of every plane.  The radial streaming shift moves values inside a pair and
-// across lanes with one shuffle per plane; the two halo columns c0 - 1 and
-// c0 + 64 are loaded by lanes 0 and 31.  The node arithmetic runs on pairs
-// with the packed FP32x2 instructions (FADD2 / FMUL2 / FFMA2) of sm_100+.
+// of every plane.  Two marches share the row update (row_tail):
+//   * march2 takes whole rows from a row source (plain loads, or a TMA ring
+//     copied into registers), carries the row groups in registers and does
+//     the radial streaming shift with one shuffle per plane, the halo
+//     columns c0 - 1 and c0 + 64 coming from lanes 0 and 31;
+//   * march3 reads the pulled values in place from a TMA ring holding rows
+//     i - 1, i and i + 1 (the radial shift is a column offset in the stage).
+// The node arithmetic runs on pairs with the packed FP32x2 instructions
+// (FADD2 / FMUL2 / FFMA2) of sm_100+.
 //
 // The arithmetic is the scalar update_node() reorganised into shared
 // subexpressions and fused multiply-adds; both follow the same equations of
@@ -392,9 +397,9 @@ template <typename S> struct RowDirect {
     __device__ __forceinline__ void finish() {}
 };
 
-// TMA ring (sm_90+ bulk tensor copies): one 3-D box per row -- kTmaCols
-// columns starting kTmaOff columns left of the warp's window, one row, all 19
-// planes -- into a stage of shared memory, completion signalled on an
+// TMA ring (sm_90+ bulk tensor copies): one 3-D box per row -- TmaGeom::cols
+// columns starting TmaGeom::off columns left of the warp's window, one row,
+// all 19 planes -- into a stage of shared memory, completion signalled on an
 // mbarrier.  Lane 0 issues the copies; every wait is bounded and a timeout
 // sets the device status word instead of spinning for ever.
 template <typename S> struct TmaGeom {
@@ -801,7 +806,7 @@ __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__
 // values are read straight from them, the radial shift being a column offset
 // (the stage holds the two halo columns).  Row i - 1 is released once its
 // e_x = +1 group is read, so that the copy of row i + 2 is in flight during
-// the step.  R stages (R >= 3) per warp.
+// the step.  R stages (R >= 3) per warp; with R = 4 one more row is in flight.
 
 template <typename S, int R> struct RowRing {
     static_assert(R >= 3, "rows i - 1, i and i + 1 must fit");
