@@ -1317,6 +1317,7 @@ Launch default_launch(const HostParams &p)
         seg = (int)((p.nz + segs - 1) / segs);
         if (seg < 4) seg = 4;
     }
+    if ((p.nz + seg - 1) / seg > 65535) seg = (p.nz + 65534) / 65535;  // grid.y limit
     l.seg_rows = seg;
     return l;
 }

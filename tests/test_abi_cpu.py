@@ -120,3 +120,21 @@ def test_create_and_parameter_validation_without_device_work(lib):
         assert lib.lb_get_step(ctx, C.byref(s)) == _abi.LB_OK and s.value == 0
     finally:
         assert lib.lb_destroy(ctx) == _abi.LB_OK
+
+
+def test_default_launch_respects_the_grid_limit_for_tall_lattices(lib):
+    """4-row segments would need more than 65535 z-blocks for nz = 400000."""
+    from paper_1806_10241_gb300 import _abi
+    from paper_1806_10241_gb300 import workloads as W
+    params = dict(W.swirling_cylinder(nr=64, nz=8).params, nz=400000)  # parameters only, no fields
+    d = _abi.make_desc(params, "fp16")
+    n = C.c_size_t()
+    assert lib.lb_required_bytes(C.byref(d), C.byref(n)) == _abi.LB_OK
+    ctx = C.c_void_p()
+    assert lib.lb_create(C.byref(d), C.c_void_p(1 << 40), n.value, None, C.byref(ctx)) == _abi.LB_OK
+    try:
+        seg, wpb, fetch = C.c_int32(), C.c_int32(), C.c_int32()
+        assert lib.lb_get_launch(ctx, C.byref(seg), C.byref(wpb), C.byref(fetch)) == _abi.LB_OK
+        assert (400000 + seg.value - 1) // seg.value <= 65535
+    finally:
+        lib.lb_destroy(ctx)
