@@ -57,28 +57,21 @@ __device__ __forceinline__ F2 sel2(bool px, bool py, F2 a, F2 b)  // per compone
 
 // ---- pair loads / stores ------------------------------------------------------
 
-// Counter-based random words for stochastic rounding.  The PCG hash of
-// Jarzynski & Olano (2020) of (node, step salt) seeds a 32-bit linear
-// congruential sequence (the quick generator of Numerical Recipes,
-// multiplier 1664525, increment 1013904223); each word is the state with its
-// high half folded onto its low half, so the bits the conversion consumes
-// (bits 0-12 and 16-28 for FP16, 0-15 and 16-31 for BF16) all carry the
-// well-mixed high bits of the state.  One multiply-add and one shift-xor per
-// word.
+// Counter-based random words for stochastic rounding: the PCG hash of
+// Jarzynski & Olano (2020) seeds a xorshift32 sequence (Marsaglia 2003).
 __device__ __forceinline__ uint32_t pcg_hash(uint32_t v)
 {
     const uint32_t s = v * 747796405u + 2891336453u;
     const uint32_t w = ((s >> ((s >> 28u) + 4u)) ^ s) * 277803737u;
     return (w >> 22u) ^ w;
 }
-struct RoundBits {
-    uint32_t s;
-    __device__ __forceinline__ uint32_t next()
-    {
-        s = s * 1664525u + 1013904223u;
-        return s ^ (s >> 16);
-    }
-};
+__device__ __forceinline__ uint32_t xorshift32(uint32_t x)
+{
+    x ^= x << 13;
+    x ^= x >> 17;
+    x ^= x << 5;
+    return x;
+}
 
 template <typename S> struct PairIO;
 template <> struct PairIO<float> {
@@ -703,21 +696,24 @@ __device__ __forceinline__ void row_tail(const KP<float> &k, const S *__restrict
 
     if (outA) {
         S *p = dst + (long long)i * k.pitch + A;
-        RoundBits rb{0u};
-        if (PairIO<S>::rounds) rb.s = pcg_hash((uint32_t)(i * k.pitch + A) ^ salt);
+        uint32_t w = 0;
+        if (PairIO<S>::rounds) w = pcg_hash((uint32_t)(i * k.pitch + A) ^ salt) | 1u;
         const F2 m = sp(Scaled<S>::value ? sc : 1.0f);
 #pragma unroll
-        for (int q = 0; q < 9; ++q)
-            PairIO<S>::st(p + q * k.plane, Scaled<S>::value ? o.f[q] * m : o.f[q],
-                          PairIO<S>::rounds ? rb.next() : 0u);
+        for (int q = 0; q < 9; ++q) {
+            if (PairIO<S>::rounds) w = xorshift32(w);
+            PairIO<S>::st(p + q * k.plane, Scaled<S>::value ? o.f[q] * m : o.f[q], w);
+        }
 #pragma unroll
-        for (int q = 0; q < 5; ++q)
-            PairIO<S>::st(p + (G0 + q) * k.plane, Scaled<S>::value ? o.g[q] * m : o.g[q],
-                          PairIO<S>::rounds ? rb.next() : 0u);
+        for (int q = 0; q < 5; ++q) {
+            if (PairIO<S>::rounds) w = xorshift32(w);
+            PairIO<S>::st(p + (G0 + q) * k.plane, Scaled<S>::value ? o.g[q] * m : o.g[q], w);
+        }
 #pragma unroll
-        for (int q = 0; q < 5; ++q)
-            PairIO<S>::st(p + (H0 + q) * k.plane, Scaled<S>::value ? o.h[q] * m : o.h[q],
-                          PairIO<S>::rounds ? rb.next() : 0u);
+        for (int q = 0; q < 5; ++q) {
+            if (PairIO<S>::rounds) w = xorshift32(w);
+            PairIO<S>::st(p + (H0 + q) * k.plane, Scaled<S>::value ? o.h[q] * m : o.h[q], w);
+        }
     }
 
 }
