@@ -204,7 +204,7 @@ def run_serving(args):
     torch.cuda.set_device(0)
     reqs = W.serving_requests(count=args.requests, rate=50.0, seed=0, nr_lo=args.nr_lo, nr_hi=args.nr_hi)
     kw = dict(steps_per_round=500, check_every=500, window=1000, tol=1e-6, max_steps=args.max_steps)
-    srv = Server(storage=args.serve_storage, graph_steps=10, **kw)
+    srv = Server(storage=args.serve_storage, graph_steps=10, autotune=True, **kw)
     rep_b = srv.run(reqs)
     rep_s = Server(storage=args.serve_storage, **kw).run_sequential(reqs, storage="fp32")
     rb, seq = rep_b.summary(), rep_s.summary()
@@ -219,7 +219,7 @@ def run_serving(args):
                                    "40 % swirling cylinder), continuous batching",
                        "requests": args.requests, "rate_per_s": 50.0, "nr": f"U{{{args.nr_lo}..{args.nr_hi}}}",
                        "nz": "nr * U{1,2}", "Ra": "log-U[1e3,1e5]", "steady": "|dNu| < 1e-6 over 1000 steps",
-                       "max_steps": args.max_steps},
+                       "max_steps": args.max_steps, "batch_launch": "autotuned per size class"},
             "p50_latency_s": rb["p50_latency_s"], "p99_latency_s": rb["p99_latency_s"],
             "nu_rel_diff_vs_sequential_fp32": {"max": float(max(dnu)) if dnu else None,
                                                "median": float(sorted(dnu)[len(dnu) // 2]) if dnu else None},

@@ -78,7 +78,7 @@ def tune_solver(solver, steps: int = 20, use_cache: bool = True) -> tuple:
 
 def tune_batch(batch, steps: int = 10, graph_steps: int = 10, use_cache: bool = True) -> tuple:
     """Pick (seg_rows, warps_per_block, row_fetch) for a batch, keyed by its node count."""
-    key = f"batch/{batch.solvers[0].storage}/{_size_class(batch.nodes)}/{len(batch.solvers)}"
+    key = f"batch/{batch.solvers[0].storage}/{_size_class(batch.nodes)}/{_size_class(len(batch.solvers))}"
     with _lock:
         cache = _load() if use_cache else {}
     if key in cache and len(cache[key]["launch"]) == 3:

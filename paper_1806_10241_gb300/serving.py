@@ -25,6 +25,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
+from .autotune import tune_batch
 from .batch import Batch
 from .solver import Solver, required_bytes
 from .workloads import Request
@@ -77,6 +78,7 @@ class _Active:
     def __init__(self, req: Request, solver: Solver, rec: Record, nbytes: int):
         self.req, self.solver, self.rec, self.nbytes = req, solver, rec, nbytes
         self.history: list[tuple[int, float]] = []  # (step, Nu)
+        self.last_check = 0  # step of the last diagnostics
 
 
 def _steady(history: list[tuple[int, float]], window: int, tol: float) -> bool:
@@ -94,7 +96,7 @@ class Server:
                  window: int = 1000, tol: float = 1e-6, max_steps: int = 200_000,
                  hbm_budget: int | None = None, reserve_bytes: int = 1 << 30, max_active: int = 512,
                  graph_steps: int = 10, seg_rows: int = 0, warps_per_block: int = 0,
-                 device: str = "cuda", keep_results: bool = False):
+                 device: str = "cuda", keep_results: bool = False, autotune: bool = False):
         if check_every % steps_per_round:
             raise ValueError("check_every must be a multiple of steps_per_round")
         self.storage = storage
@@ -107,6 +109,7 @@ class Server:
         self.graph_steps = graph_steps
         self.seg_rows = seg_rows
         self.warps_per_block = warps_per_block
+        self.autotune = autotune
         self.device = torch.device(device)
         self.keep_results = keep_results
         self.results: dict[int, np.ndarray] = {}  # final distributions (keep_results)
@@ -132,6 +135,7 @@ class Server:
         when it is finished."""
         if d is None:
             d = a.solver.diag()
+        a.last_check = d["step"]
         a.rec.steps = d["step"]
         a.rec.nu = d["nu_avg"]
         a.history.append((d["step"], d["nu_avg"]))
@@ -192,15 +196,16 @@ class Server:
                     batch.close()
                 batch = Batch([a.solver for a in active], stream=self.stream, seg_rows=self.seg_rows,
                               warps_per_block=self.warps_per_block, graph_steps=self.graph_steps)
+                if self.autotune:  # cached per storage and size class; tuning steps are real steps
+                    tune_batch(batch, steps=3, graph_steps=self.graph_steps)
                 dirty = False
             batch.step(self.steps_per_round)
             rounds += 1
-            # every lattice of the batch has taken the same number of rounds
-            # since its admission; check those at a multiple of check_every
+            # diagnostics of the lattices whose last check is check_every steps back
             if on_round is not None:
                 on_round(self, clock() - t0)
             finished = []
-            due = [a.solver.step_count % self.check_every == 0 for a in active]
+            due = [a.solver.step_count - a.last_check >= self.check_every for a in active]
             diags = batch.diag() if any(due) else None  # every lattice's diagnostics in one download
             for a, is_due, d in zip(active, due, diags or [None] * len(active)):
                 if a.rec.rid in self._cancelled:
@@ -245,7 +250,7 @@ class Server:
             rec.admitted = clock() - t0
             while True:
                 s.step(self.steps_per_round)
-                if s.step_count % self.check_every == 0 and self._check(a):
+                if s.step_count - a.last_check >= self.check_every and self._check(a):
                     break
             rec.finished = clock() - t0
             s.close()

@@ -132,3 +132,22 @@ def test_diverged_lattice_is_reported_and_retired():
     st = {r.rid: r.status for r in rep.records}
     assert st[0] == "diverged"
     assert st[1] in ("converged", "capped") and st[2] in ("converged", "capped")
+
+
+def test_autotuned_server_gives_the_same_results_as_solo_runs():
+    """Autotuning rebuilds of the batch changes launches and adds real steps;
+    each request's result is still bitwise the one of its solo run for the
+    same number of steps."""
+    from paper_1806_10241_gb300 import autotune
+    from paper_1806_10241_gb300.serving import Server
+    from paper_1806_10241_gb300.solver import Solver
+    reqs = _stream(4)
+    srv = Server(storage="fp32", steps_per_round=100, check_every=200, window=400, tol=1e-9, max_steps=600,
+                 keep_results=True, autotune=True)
+    rep = srv.run(reqs)
+    for r in rep.records:
+        req = reqs[r.rid]
+        s = Solver(req.case.params, storage="fp32")
+        s.init_fields(req.case.fields)
+        s.step(r.steps)
+        assert np.array_equal(srv.results[r.rid], s.get_dist()), r.rid
