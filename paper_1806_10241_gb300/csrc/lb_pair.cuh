@@ -937,38 +937,9 @@ __device__ __forceinline__ void march3(const KP<float> &k, const S *__restrict__
     const Lane2 L = lane2(k, c0);
     const int lane = L.lane, nz = k.nz;
     constexpr int O = TmaGeom<S>::off;
+    const int hc = lane == 0 ? O - 1 : O + 64;  // halo column of lanes 0 / 31
     const int first = (row_s > 0 || k.xper) ? row_s - 1 : row_s;
     StageRd<S> rd{nullptr, O + 2 * lane, k.inv_scale};
-
-    // Stored-state fields of the halo columns c0 - 1 (even lanes) and
-    // c0 + 64 (odd lanes) for 16 rows of the march at a time (lane l: row
-    // first + hbase + l / 2), read from global memory; lanes 0 and 31, the
-    // only users, take theirs by shuffle.  Columns outside the lattice are
-    // clamped: the wall and axis ghosts replace their fields.
-    float hx_ux = 0.0f, hx_uy = 0.0f, hx_ut = 0.0f, hx_T = 0.0f;
-    int hbase = -16;
-    const int hxcol = (lane & 1) ? min(c0 + 64, k.nr - 1) : max(c0 - 1, 0);
-    auto halo_at = [&](int r, float &ux, float &uy, float &ut, float &T) {  // r: row - first
-        if (r - hbase >= 16) {
-            hbase = r;
-            int row = first + hbase + (lane >> 1);
-            row = row >= nz ? row - nz : (row < 0 ? row + nz : row);
-            row = row < 0 ? 0 : (row >= nz ? nz - 1 : row);
-            const S *p = src + (long long)row * k.pitch + hxcol;
-            float h[NQ];
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                h[q] = Cvt<S, float>::ld(p + q * k.plane);
-                if (Scaled<S>::value) h[q] *= k.inv_scale;
-            }
-            halo_fields(k, h, hx_ux, hx_uy, hx_ut, hx_T);
-        }
-        const int from = 2 * (r - hbase) + (lane == 31 ? 1 : 0);
-        ux = __shfl_sync(FULL, hx_ux, from);
-        uy = __shfl_sync(FULL, hx_uy, from);
-        ut = __shfl_sync(FULL, hx_ut, from);
-        T = __shfl_sync(FULL, hx_T, from);
-    };
 
     // stored-state fields of row row_s (and u_y of row row_s - 1)
     PM2 pm_cur;
@@ -977,6 +948,7 @@ __device__ __forceinline__ void march3(const KP<float> &k, const S *__restrict__
     {
         if (!rs.wait_upto(row_s - first)) return rs.finish();
         F2 v[NQ];
+        float hv[NQ];
         if (row_s > first) {
             rd.b = rs.stage(0);
 #pragma unroll
@@ -985,9 +957,12 @@ __device__ __forceinline__ void march3(const KP<float> &k, const S *__restrict__
         }
         rd.b = rs.stage(row_s - first);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) v[q] = rd.pair(q);
+        for (int q = 0; q < NQ; ++q) {
+            v[q] = rd.pair(q);
+            hv[q] = rd.col(q, hc);
+        }
         pm_cur = moments2(v, k);
-        halo_at(row_s - first, pmh_ux, pmh_uy, pmh_ut, pmh_T);
+        halo_fields(k, hv, pmh_ux, pmh_uy, pmh_ut, pmh_T);
     }
 
     for (int i = row_s; i < row_e; ++i) {
@@ -1026,10 +1001,14 @@ __device__ __forceinline__ void march3(const KP<float> &k, const S *__restrict__
         if (has_p) {
             rd.b = rs.stage(t + 1);
             F2 v[NQ];
+            float hv[NQ];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) v[q] = rd.pair(q);
+            for (int q = 0; q < NQ; ++q) {
+                v[q] = rd.pair(q);
+                hv[q] = rd.col(q, hc);
+            }
             pm_n = moments2(v, k);
-            halo_at(t + 1, nh_ux, nh_uy, nh_ut, nh_T);
+            halo_fields(k, hv, nh_ux, nh_uy, nh_ut, nh_T);
             fv[3] = v[3];
             fv[6] = rd.left(6);
             fv[7] = rd.right(7);
