@@ -16,7 +16,7 @@
  * Distributions are stored as absolute FP64 values, array-of-structures
  * per node (f[9], g[5], h[5]), node index = z * nr + r.
  *
- * Readings of the paper where it is silent or garbled (listed in the design doc):
+ * Readings of the paper where it is silent or garbled:
  *   - Eq. 34 and 49 print "+(ux^2+uy^2)psi" and "+(ux^2-uy^2)psi"; with that
  *     sign the D2Q5 equilibrium is not a fixed point.  The default uses the
  *     sign obtained by relaxing the central moments (minus); sign_literal=1
