@@ -697,7 +697,7 @@ __device__ __forceinline__ void row_tail(const KP<float> &k, const S *__restrict
     if (outA) {
         S *p = dst + (long long)i * k.pitch + A;
         uint32_t w = 0;
-        if (PairIO<S>::rounds) w = pcg_hash((uint32_t)(i * k.pitch + A) ^ salt) | 1u;
+        if (PairIO<S>::rounds) w = pcg_hash(((uint32_t)i * (uint32_t)k.pitch + (uint32_t)A) ^ salt) | 1u;
         const F2 m = sp(Scaled<S>::value ? sc : 1.0f);
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
