@@ -84,6 +84,7 @@ def lib():
                 getattr(L, name).argtypes = [C.c_void_p, dp]
             L.orc_step.argtypes = [C.c_void_p, C.c_int]
             L.orc_diag_compute.argtypes = [C.c_void_p, C.POINTER(Diag)]
+            L.orc_stream_function.argtypes = [C.c_void_p, dp, dp]
             L.orc_get_step.restype = C.c_int64
             L.orc_get_step.argtypes = [C.c_void_p]
             L.orc_eq_d2q9.argtypes = [C.c_double, C.c_double, C.c_double, dp]
@@ -191,6 +192,13 @@ class Oracle:
         return {"nu_side": list(d.nu_side), "nu_i": d.nu_i, "nu_o": d.nu_o,
                 "nu_avg": d.nu_avg, "mass": d.mass, "mass_r": d.mass_r,
                 "T_sum": d.T_sum, "u_max": d.u_max, "step": int(d.step)}
+
+    def stream_function(self) -> tuple:
+        """(psi [nz, nr] on the cell faces y = r0 + j + 1, max |psi|)."""
+        a = np.empty((self.nz, self.nr), np.float64)
+        m = C.c_double()
+        lib().orc_stream_function(self._h, _dp(a), C.byref(m))
+        return a, m.value
 
     @property
     def step_count(self) -> int:

@@ -620,6 +620,32 @@ int orc_fields(const orc_state *s, double *fields)
 
 /* ---- diagnostics ------------------------------------------------------ */
 
+/* Stream function of the meridian flow (Sec. 3.6): dPsi/dy = -y u_x,
+ * dPsi/dx = y u_y, Psi = 0 on the inner boundary (axis or inner wall, at
+ * y = r0).  Integrated along y with the midpoint rule over whole cells, so
+ * psi[i][j] is Psi on the cell face y = r0 + j + 1 of row i:
+ * psi[i][j] = -sum_{j' <= j} y_j' u_x(i, j').  Fields of the pre-collision
+ * state; psi may be NULL; *psi_max = max |Psi|. */
+int orc_stream_function(const orc_state *s, double *psi, double *psi_max)
+{
+    const orc_params *p = &s->p;
+    precollision_fields(s);
+    const double *ux = s->Gn + 1 * s->n;
+    double m = 0.0;
+    for (int i = 0; i < p->nz; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < p->nr; ++j) {
+            const double y = p->r0 + j + 0.5;
+            acc -= y * ux[(size_t)i * p->nr + j];
+            if (psi) psi[(size_t)i * p->nr + j] = acc;
+            if (fabs(acc) > m) m = fabs(acc);
+        }
+    }
+    *psi_max = m;
+    return 0;
+}
+
+
 /* Nusselt numbers (Sec. 3.2): Nu = -R_w / (H dT) int dT/dy dx on a lateral
  * wall of radius R_w.  On an end wall the heat flux is averaged over the
  * wall area: Nu = -(H / dT) (2 / (R_o^2 - R_i^2)) int dT/dx r dr.  The wall

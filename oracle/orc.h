@@ -102,6 +102,9 @@ int orc_step(orc_state *s, int nsteps);
  * collision uses, [5][nz][nr] rho, u_x, u_y, u_theta, T */
 int orc_fields(const orc_state *s, double *fields);
 int orc_diag_compute(const orc_state *s, orc_diag *out);
+/* stream function on the cell faces y = r0 + j + 1, [nz][nr] (may be NULL),
+ * and max |Psi| */
+int orc_stream_function(const orc_state *s, double *psi, double *psi_max);
 int64_t orc_get_step(const orc_state *s);
 
 /* per-node building blocks (exported for the brute-force pins) */

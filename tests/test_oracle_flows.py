@@ -116,6 +116,29 @@ def test_hagen_poiseuille_second_order():
     assert min(p) > 1.7, (errs, p)
 
 
+def test_stream_function_of_poiseuille_flow_second_order():
+    """Stream function (Sec. 3.6, dPsi/dy = -y u_x) of pipe flow:
+    Psi(r) = -G (R^2 r^2 / 2 - r^4 / 4) / (4 mu), |Psi|max = G R^4 / (16 mu)
+    at the wall; it must also equal the midpoint sum of the oracle's own
+    velocity profile face by face."""
+    errs = []
+    for R in (8, 16, 32):
+        G = 1e-4 / R**2
+        case = W.hagen_poiseuille(R=R, G=G, tau=0.8)
+        o, fl = run_steady(case, tol=1e-12)
+        psi, pmax = o.stream_function()
+        mu = case.params["nu"] * case.params["rho0"]
+        faces = np.arange(1, R + 1, dtype=np.float64)  # r of the cell faces
+        exact = -G * (R * R * faces**2 / 2 - faces**4 / 4) / (4 * mu)
+        errs.append(rel_l2(psi[1], exact))
+        assert pmax == pytest.approx(np.max(np.abs(psi)))
+        assert pmax == pytest.approx(G * R**4 / (16 * mu), rel=0.02)
+        r = W.radii(R, 0.0)
+        assert np.allclose(psi[1], -np.cumsum(r * fl[1, 1]), rtol=1e-12, atol=0)
+    p = order(errs)
+    assert min(p) > 1.7, (errs, p)
+
+
 # ---- conduction ---------------------------------------------------------------
 
 def test_annular_conduction_profile_and_nusselt():
