@@ -171,6 +171,14 @@ LB_EXPORT lb_status lb_get_fields(lb_ctx *ctx, double *host_fields);
  * bounded wait of a step kernel ran out (the state is then not valid). */
 LB_EXPORT lb_status lb_diagnostics(lb_ctx *ctx, lb_diag *out);
 
+/* Stream function of the meridian flow (Sec. 3.6: dPsi/dy = -y u_x,
+ * dPsi/dx = y u_y), Psi = 0 on the inner boundary (axis or inner wall),
+ * integrated along y with the midpoint rule from the pre-collision fields:
+ * host_psi[nz][nr] (may be NULL) holds Psi on the cell faces y = r0 + j + 1,
+ * *psi_max = max |Psi| (FP64).  Synchronises the stream; uses the idle
+ * distribution buffer as scratch. */
+LB_EXPORT lb_status lb_stream_function(lb_ctx *ctx, double *host_psi, double *psi_max);
+
 /* Distributions as absolute values, host [19][nz][nr] doubles: f0..f8,
  * g0..g4, h0..h4 (velocity order of Eq. 10 and Eq. 28).  Synchronous. */
 LB_EXPORT lb_status lb_get_distributions(lb_ctx *ctx, double *host19);

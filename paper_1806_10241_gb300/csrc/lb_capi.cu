@@ -340,6 +340,38 @@ lb_status lb_get_fields(lb_ctx *ctx, double *host_fields)
     return LB_OK;
 }
 
+lb_status lb_stream_function(lb_ctx *ctx, double *host_psi, double *psi_max)
+{
+    lb_status st = need_params(ctx);
+    if (st != LB_OK) return st;
+    if (!psi_max) return fail(ctx, LB_ERR_ARG, "psi_max is NULL");
+    double *stage;
+    int rows;
+    if ((st = staging(ctx, 5, &stage, &rows)) != LB_OK) return st;
+    const int nr = ctx->hp.nr, nz = ctx->hp.nz;
+    std::vector<double> rowmax((size_t)nz);
+    for (int r0 = 0; r0 < nz; r0 += rows) {
+        const int r1 = r0 + rows < nz ? r0 + rows : nz;
+        const size_t n = (size_t)(r1 - r0) * nr;
+        // fields into planes 0..4 of the stage; Psi over plane 0, row maxima over plane 2
+        cudaError_t e = lbk::launch_fields(ctx->hp, ctx->launch, ctx->dist[ctx->cur], stage, r0, r1, ctx->stream);
+        if (e == cudaSuccess)
+            e = lbk::launch_psi(stage + n, stage, stage + 2 * n, r1 - r0, nr, ctx->hp.r0, ctx->stream);
+        if (e == cudaSuccess && host_psi)
+            e = cudaMemcpyAsync(host_psi + (size_t)r0 * nr, stage, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(rowmax.data() + r0, stage + 2 * n, (size_t)(r1 - r0) * sizeof(double),
+                                cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "stream function");
+    }
+    double m = 0.0;
+    for (double v : rowmax) m = v > m ? v : m;
+    *psi_max = m;
+    return LB_OK;
+}
+
 // lb_diag from the NSUM device sums of the diagnostics and the status word
 static void fill_diag(const lb_ctx *ctx, const double *res, int kstatus, lb_diag *out)
 {

@@ -45,6 +45,10 @@ cudaError_t make_tensor_map(const HostParams &p, void *buf, void *map_out);
 // Pre-collision fields of rows [row0, row1) into out[5][row1-row0][nr] (double).
 cudaError_t launch_fields(const HostParams &p, const Launch &l, const void *src, double *out,
                           int row0, int row1, cudaStream_t s);
+// Stream function of nrows rows from their axial velocity ux[nrows][nr]
+// (pre-collision fields): psi[nrows][nr] on the cell faces y = r0 + j + 1
+// (psi may be null) and rowmax[nrows] = max |Psi| per row.
+cudaError_t launch_psi(const double *ux, double *psi, double *rowmax, int nrows, int nr, double r0, cudaStream_t s);
 // Diagnostics of the stored state src: block partial sums (partial), the
 // pre-collision T field (tfield, nz * nr doubles of scratch) and the final
 // values in result[NSUM]: 0 sum(rho - rho0), 1 sum((rho - rho0) y), 2 sum T,

@@ -785,6 +785,37 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG)
     march3<S, R>(k, src, dst, warp * 64, s, e, salt, rs);
 }
 
+// Stream function of the meridian flow (Sec. 3.6): dPsi/dy = -y u_x with
+// Psi = 0 on the inner boundary y = r0, midpoint sums over whole cells, so
+// psi[i][j] is Psi on the face y = r0 + j + 1 of row i.  One warp per row:
+// an FP64 warp scan per 32 columns plus the carry; rowmax[i] = max |Psi|.
+__global__ void __launch_bounds__(128) k_psi(const double *__restrict__ ux, double *__restrict__ psi,
+                                             double *__restrict__ rowmax, int nrows, int nr, double r0)
+{
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= nrows) return;
+    const int lane = threadIdx.x & 31;
+    double carry = 0.0, m = 0.0;
+    for (int j0 = 0; j0 < nr; j0 += 32) {
+        const int j = j0 + lane;
+        double v = j < nr ? -(r0 + j + 0.5) * ux[(long long)row * nr + j] : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double w = __shfl_up_sync(FULL, v, o);
+            if (lane >= o) v += w;
+        }
+        v += carry;
+        if (j < nr) {
+            if (psi) psi[(long long)row * nr + j] = v;
+            m = fmax(m, fabs(v));
+        }
+        carry = __shfl_sync(FULL, v, 31);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(FULL, m, o));
+    if (lane == 0) rowmax[row] = m;
+}
+
 constexpr int kFieldRows = 32;  // rows per z-segment of the field export
 
 template <typename S, typename C>
@@ -1362,6 +1393,13 @@ cudaError_t make_tensor_map(const HostParams &p, void *buf, void *map_out)
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_psi(const double *ux, double *psi, double *rowmax, int nrows, int nr, double r0, cudaStream_t s)
+{
+    if (nrows < 1) return cudaSuccess;
+    k_psi<<<(nrows + 3) / 4, 128, 0, s>>>(ux, psi, rowmax, nrows, nr, r0);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fields(const HostParams &p, const Launch &l, const void *src, double *out, int row0, int row1,

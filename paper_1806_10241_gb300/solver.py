@@ -118,6 +118,13 @@ class Solver:
         self._check(self.L.lb_diagnostics(self.ctx, C.byref(d)))
         return diag_dict(d)
 
+    def stream_function(self, field: bool = False) -> tuple:
+        """(psi [nz, nr] on the cell faces y = r0 + j + 1 or None, max |psi|)."""
+        a = np.empty((self.nz, self.nr), np.float64) if field else None
+        m = C.c_double()
+        self._check(self.L.lb_stream_function(self.ctx, _dptr(a) if field else None, C.byref(m)))
+        return a, m.value
+
     def get_dist(self) -> np.ndarray:
         a = np.empty((19, self.nz, self.nr), np.float64)
         self._check(self.L.lb_get_distributions(self.ctx, _dptr(a)))

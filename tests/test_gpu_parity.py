@@ -266,3 +266,22 @@ def test_far_corner_of_a_lattice_beyond_4_gib_matches_a_small_copy():
     want = o.fields()
     for q in (1, 2, 3, 4):
         assert np.max(np.abs(got[q] - want[q])) < 1e-6, q
+
+
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_stream_function_matches_oracle(storage, tol):
+    """Stream function (Sec. 3.6) of a heated swirling cylinder and of an
+    annulus (inner boundary: the axis, an inner wall) after 300 steps."""
+    for c in (W.swirling_cylinder(nr=70, nz=96, Re=200.0, Ra=1e5, amp=1e-3, seed=3),
+              W.annulus_convection(nr=45, nz=61, Ra=1e5, amp=1e-3, seed=4, swirl_inner=0.01)):
+        g = Solver(c.params, storage=storage)
+        g.init_fields(c.fields)
+        g.step(300)
+        o = oracle.Oracle(c.params)
+        o.init_fields(c.fields)
+        o.step(300)
+        psi, pmax = g.stream_function(field=True)
+        want, wmax = o.stream_function()
+        assert _rel_l2(psi, want) < tol, (c.name, _rel_l2(psi, want))
+        assert pmax == pytest.approx(wmax, rel=tol)
+        assert g.stream_function()[1] == pmax  # without the field: the same maximum
