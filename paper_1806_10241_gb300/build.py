@@ -44,7 +44,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     procs, objs = [], []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        # per-process object names: concurrent builds (one per rank) never share a file
+        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + f".{os.getpid()}.o")
         cmd = [NVCC, *ARCH, *FLAGS, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
         if verbose:
             cmd.append("-Xptxas=-v")
@@ -61,7 +62,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError("nvcc failed for " + ", ".join(failed))
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs], check=True)
-    os.replace(tmp, LIB)
+    os.replace(tmp, LIB)  # atomic: a concurrent loader sees the old or the new library
+    for o in objs:
+        os.remove(o)
     return LIB
 
 
