@@ -285,3 +285,39 @@ def test_stream_function_matches_oracle(storage, tol):
         assert _rel_l2(psi, want) < tol, (c.name, _rel_l2(psi, want))
         assert pmax == pytest.approx(wmax, rel=tol)
         assert g.stream_function()[1] == pmax  # without the field: the same maximum
+
+
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+W5 = np.array([1 / 3] + [1 / 6] * 4)
+
+
+def _ulp16(x, mant_bits):
+    """Spacing of a 16-bit float format with `mant_bits` stored mantissa bits
+    at |x| (normal range)."""
+    e = np.floor(np.log2(np.maximum(np.abs(x), 1e-30)))
+    return np.exp2(e - mant_bits)
+
+
+@pytest.mark.parametrize("storage,mant,scale", [("fp16", 10, 1024.0), ("bf16", 7, 1.0)])
+@pytest.mark.parametrize("name", ["annulus_walls", "cylinder_axis", "periodic_annulus"])
+def test_16bit_distributions_after_one_step_within_one_rounding(name, storage, mant, scale):
+    """One step from a state the 16-bit buffer holds exactly: every stored
+    value equals the oracle's to within one stochastic rounding of its
+    deviation from the rest state (one 16-bit spacing) plus the FP32
+    arithmetic (2e-6)."""
+    params = BUILDERS[name](61, 13)
+    g = Solver(params, storage=storage)
+    g.set_dist(random_state(params, seed=17))
+    start = g.get_dist()  # the state as stored in 16 bits
+    g.step(1)
+    got = g.get_dist()
+    o = oracle.Oracle(params)
+    o.set_dist(start)
+    o.step(1)
+    want = o.get_dist()
+    rest = np.concatenate([W9 * params["rho0"], np.zeros(5), W5 * params["T0"]])[:, None, None]
+    mag = np.maximum(np.abs(want - rest), np.abs(got - rest))  # spacing of the larger binade
+    tol = _ulp16(mag * scale, mant) / scale + 2e-6
+    assert np.all(np.abs(got - want) <= tol), float(np.max(np.abs(got - want) / tol))
+    # the roundings are unbiased: their mean over the lattice is far below one spacing
+    assert abs(np.mean((got - want) / tol)) < 0.05
