@@ -79,7 +79,7 @@ def planar_box(nr, nz):
 BUILDERS = {"annulus_walls": annulus_walls, "cylinder_axis": cylinder_axis,
             "periodic_annulus": periodic_annulus, "periodic_cylinder": periodic_cylinder,
             "planar_box": planar_box}
-SIZES = [(2, 2), (7, 9), (31, 5), (33, 17), (61, 13), (97, 33)]
+SIZES = [(2, 2), (7, 9), (31, 5), (33, 17), (61, 13), (65, 7), (97, 33), (128, 4)]
 
 
 def random_state(params, seed):
