@@ -171,6 +171,14 @@ LB_EXPORT lb_status lb_get_fields(lb_ctx *ctx, double *host_fields);
  * bounded wait of a step kernel ran out (the state is then not valid). */
 LB_EXPORT lb_status lb_diagnostics(lb_ctx *ctx, lb_diag *out);
 
+/* Self-test of the failure path of the bounded device waits (no counterpart
+ * in the paper): a kernel polls, `polls` times (1..2^22), an mbarrier that
+ * nothing arrives at -- the same bounded wait the TMA row rings use -- and
+ * sets the context's status word to LB_ERR_TIMEOUT, which the next
+ * lb_diagnostics reports; lb_set_params clears it.  No fault, trap or hang:
+ * the context stays usable.  Synchronises the stream. */
+LB_EXPORT lb_status lb_selftest_timeout(lb_ctx *ctx, int32_t polls);
+
 /* Stream function of the meridian flow (Sec. 3.6: dPsi/dy = -y u_x,
  * dPsi/dx = y u_y), Psi = 0 on the inner boundary (axis or inner wall),
  * integrated along y with the midpoint rule from the pre-collision fields:

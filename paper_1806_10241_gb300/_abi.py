@@ -72,6 +72,7 @@ PROTOTYPES = {
     "lb_batch_required_bytes": (_st, [C.c_int32, C.POINTER(C.c_size_t)]),
     "lb_batch_create": (_st, [C.POINTER(_vp), C.c_int32, _vp, C.c_size_t, _vp, C.POINTER(_vp)]),
     "lb_batch_set_launch": (_st, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    "lb_selftest_timeout": (_st, [_vp, C.c_int32]),
     "lb_stream_function": (_st, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lb_batch_step": (_st, [_vp, C.c_int32]),
     "lb_batch_diagnostics": (_st, [_vp, _vp]),

@@ -340,6 +340,17 @@ lb_status lb_get_fields(lb_ctx *ctx, double *host_fields)
     return LB_OK;
 }
 
+lb_status lb_selftest_timeout(lb_ctx *ctx, int32_t polls)
+{
+    lb_status st = need_params(ctx);
+    if (st != LB_OK) return st;
+    if (polls < 1 || polls > (1 << 22)) return fail(ctx, LB_ERR_ARG, "1 <= polls <= 2^22");
+    cudaError_t e = lbk::launch_wait_selftest(ctx->status, polls, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "wait self-test");
+    return LB_OK;
+}
+
 lb_status lb_stream_function(lb_ctx *ctx, double *host_psi, double *psi_max)
 {
     lb_status st = need_params(ctx);

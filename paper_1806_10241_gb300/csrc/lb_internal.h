@@ -45,6 +45,9 @@ cudaError_t make_tensor_map(const HostParams &p, void *buf, void *map_out);
 // Pre-collision fields of rows [row0, row1) into out[5][row1-row0][nr] (double).
 cudaError_t launch_fields(const HostParams &p, const Launch &l, const void *src, double *out,
                           int row0, int row1, cudaStream_t s);
+// Bounded-wait self-test: a warp polls an mbarrier nothing arrives at,
+// `polls` times, and sets *status to LB_ERR_TIMEOUT.
+cudaError_t launch_wait_selftest(int *status, int polls, cudaStream_t s);
 // Stream function of nrows rows from their axial velocity ux[nrows][nr]
 // (pre-collision fields): psi[nrows][nr] on the cell faces y = r0 + j + 1
 // (psi may be null) and rowmax[nrows] = max |Psi| per row.

@@ -1236,6 +1236,23 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restric
     }
 }
 
+// Self-test of the bounded waits: one warp waits on an mbarrier that nothing
+// arrives at, for `polls` polls of the same bounded wait the TMA rings use;
+// the timeout must reach the status word as it does for a row that never
+// arrives.  Nothing is in flight when the kernel ends.
+__global__ void k_wait_selftest(int *status, int polls)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const bool ok = mbar_wait_bounded(b, 0u, polls);
+    if (!__all_sync(FULL, ok) && threadIdx.x == 0) atomicExch(status, (int)LB_ERR_TIMEOUT);
+}
+
 int nwindows2(int nr) { return (nr + 63) / 64; }
 
 // random bits of the stochastic rounding differ from step to step
@@ -1393,6 +1410,12 @@ cudaError_t make_tensor_map(const HostParams &p, void *buf, void *map_out)
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_wait_selftest(int *status, int polls, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 32, 0, s>>>(status, polls);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_psi(const double *ux, double *psi, double *rowmax, int nrows, int nr, double r0, cudaStream_t s)

@@ -412,6 +412,20 @@ template <typename S> struct TmaGeom {
 constexpr int kTmaStages = 3;
 constexpr int kTmaWaitLimit = 1 << 22;  // bounded mbarrier polls (about a second)
 
+// Poll the mbarrier at shared address bar for the phase of the given parity
+// at most `limit` times; false when it did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int limit)
+{
+    uint32_t ok = 0;
+    for (int it = 0; it < limit && !ok; ++it)
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 template <typename S> struct RowTma {
@@ -451,16 +465,7 @@ template <typename S> struct RowTma {
 
     __device__ __forceinline__ bool wait_stage(int t)
     {
-        const int st = t % kTmaStages;
-        const uint32_t parity = (uint32_t)((t / kTmaStages) & 1);
-        uint32_t ok = 0;
-        for (int it = 0; it < kTmaWaitLimit && !ok; ++it)
-            asm volatile(
-                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                : "=r"(ok)
-                : "r"(bar_s + 8u * st), "r"(parity)
-                : "memory");
-        return ok != 0;
+        return mbar_wait_bounded(bar_s + 8u * (t % kTmaStages), (uint32_t)((t / kTmaStages) & 1), kTmaWaitLimit);
     }
 
     __device__ __forceinline__ bool get(F2 v[NQ], float hv[NQ])
@@ -847,15 +852,7 @@ template <typename S, int R> struct RowRing {
 
     __device__ __forceinline__ bool wait_one(int t)
     {
-        const uint32_t bar = bar_s + 8u * (t % R), parity = (uint32_t)((t / R) & 1);
-        uint32_t ok = 0;
-        for (int it = 0; it < kTmaWaitLimit && !ok; ++it)
-            asm volatile(
-                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                : "=r"(ok)
-                : "r"(bar), "r"(parity)
-                : "memory");
-        return ok != 0;
+        return mbar_wait_bounded(bar_s + 8u * (t % R), (uint32_t)((t / R) & 1), kTmaWaitLimit);
     }
 
     // rows up to sequence index t have landed (false after a timeout, with

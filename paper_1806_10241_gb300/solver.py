@@ -97,6 +97,11 @@ class Solver:
         self._check(self.L.lb_get_launch(self.ctx, C.byref(s), C.byref(w), C.byref(f)))
         return s.value, w.value, f.value
 
+    def reset(self) -> None:
+        """lb_set_params again: the state returns to rest at step 0 and the
+        device status word is cleared."""
+        self._check(self.L.lb_set_params(self.ctx, C.byref(self._p)))
+
     def init_fields(self, fields: np.ndarray) -> None:
         a = np.ascontiguousarray(fields, np.float64).reshape(5, self.nz, self.nr)
         self._check(self.L.lb_init_fields(self.ctx, _dptr(a)))
