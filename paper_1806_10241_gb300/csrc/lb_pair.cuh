@@ -410,7 +410,11 @@ template <typename S> struct TmaGeom {
     static constexpr int stage_bytes = (box_bytes + 127) / 128 * 128;
 };
 constexpr int kTmaStages = 3;
-constexpr int kTmaWaitLimit = 1 << 22;  // bounded mbarrier polls (about a second)
+// Bounded mbarrier polls of a row wait: a poll of a phase that does not
+// complete returns after about 4 us on GB300 (measured by
+// lb_selftest_timeout), so 2^18 polls give up after about a second; a row in
+// flight normally completes within a few polls.
+constexpr int kTmaWaitLimit = 1 << 18;
 
 // Poll the mbarrier at shared address bar for the phase of the given parity
 // at most `limit` times; false when it did not complete.

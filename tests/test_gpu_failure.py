@@ -37,8 +37,8 @@ def test_bounded_wait_timeout_reaches_the_status_word_and_the_context_survives()
     _abi.check(s.L.lb_selftest_timeout(s.ctx, 64))
     per_poll = (time.perf_counter() - t) / 64
     assert s.diag()["status"] == _abi.LB_ERR_TIMEOUT
-    # 2^22 polls (the limit of the row waits) must end in minutes, not hang
-    assert per_poll * (1 << 22) < 600.0, per_poll
+    # 2^18 polls (the limit of the row waits) must end within seconds
+    assert per_poll * (1 << 18) < 10.0, per_poll
     assert s.L.lb_selftest_timeout(s.ctx, 0) == _abi.LB_ERR_ARG
     # the context stays usable: a reset clears the status and steps run again
     s.reset()  # lb_set_params: rest state, status cleared
