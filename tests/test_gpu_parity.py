@@ -321,3 +321,19 @@ def test_16bit_distributions_after_one_step_within_one_rounding(name, storage, m
     assert np.all(np.abs(got - want) <= tol), float(np.max(np.abs(got - want) / tol))
     # the roundings are unbiased: their mean over the lattice is far below one spacing
     assert abs(np.mean((got - want) / tol)) < 0.05
+
+
+@pytest.mark.parametrize("switch", ["sign_literal", "explicit_sources"])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+def test_reading_switches_match_oracle(switch, storage, tol):
+    """The printed D2Q5 sign (Eq. 34, 49) and the literal explicit source
+    evaluation (Eq. 21) as alternatives to the default readings: the GPU
+    follows the oracle with either switch on."""
+    for build in (annulus_walls, cylinder_axis):
+        params = dict(build(45, 21), **{switch: 1})
+        st = random_state(params, seed=23)
+        got, want, _, _ = run_both(params, st, 5, storage)
+        assert np.max(np.abs(got - want)) < tol, (switch, build.__name__)
+        # and the switch changes the result (it is not ignored)
+        base, _, _, _ = run_both(build(45, 21), st, 5, storage)
+        assert np.max(np.abs(base - got)) > 1e-9
