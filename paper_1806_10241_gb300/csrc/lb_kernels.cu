@@ -651,9 +651,6 @@ __device__ __forceinline__ void march(const KP<C> &k, const S *__restrict__ src,
 
 #include "lb_pair.cuh"
 
-#ifndef LB_STEP_MAXREG
-#define LB_STEP_MAXREG 128
-#endif
 template <typename S, typename C>
 __device__ __forceinline__ void step_body(const KP<C> &k, const S *__restrict__ src, S *__restrict__ dst,
                                           int seg_rows, int nwin)
@@ -666,16 +663,7 @@ __device__ __forceinline__ void step_body(const KP<C> &k, const S *__restrict__ 
     march<S, C, MODE_STEP>(k, src, dst, nullptr, 0, 0, c, s, e, nullptr);
 }
 
-// FP32-compute step (FP32 / BF16 / FP16 storage): register cap for 24
-// resident warps per SM without spills
-template <typename S, typename C>
-__global__ void __maxnreg__(LB_STEP_MAXREG) k_step(KP<C> k, const S *__restrict__ src, S *__restrict__ dst,
-                                                   int seg_rows, int nwin)
-{
-    step_body<S, C>(k, src, dst, seg_rows, nwin);
-}
-
-// FP64 step: twice the registers per value
+// FP64 step (the GPU FP64 reference path): the scalar march, 30 columns per warp
 template <typename S, typename C>
 __global__ void __maxnreg__(255) k_step64(KP<C> k, const S *__restrict__ src, S *__restrict__ dst,
                                           int seg_rows, int nwin)
