@@ -540,6 +540,7 @@ def main():
     traffic = counters_for(key)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
+                "frac_of_nominal_7900_GBs": round(achieved / 7900.0, 4),
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_node": bpn,

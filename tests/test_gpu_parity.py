@@ -337,3 +337,23 @@ def test_reading_switches_match_oracle(switch, storage, tol):
         # and the switch changes the result (it is not ignored)
         base, _, _, _ = run_both(build(45, 21), st, 5, storage)
         assert np.max(np.abs(base - got)) > 1e-9
+
+
+def test_small_annulus_case_fp64_20000_steps_matches_oracle():
+    """The small annulus case run in full: 41 x 41, R_o/R_i = 2, H = L,
+    Ra = 1e3, Pr = 0.7, FP64 storage, 20000 steps; the average inner-wall
+    Nusselt number and every field against the oracle."""
+    c = W.config_annulus_41()
+    g = Solver(c.params, storage="fp64")
+    g.init_fields(c.fields)
+    g.step(20000)
+    o = oracle.Oracle(c.params)
+    o.init_fields(c.fields)
+    o.step(20000)
+    dg, do = g.diag(), o.diag()
+    assert dg["status"] == 0
+    assert dg["nu_i"] == pytest.approx(do["nu_i"], rel=1e-10)
+    assert dg["nu_o"] == pytest.approx(do["nu_o"], rel=1e-10)
+    assert np.max(np.abs(g.fields() - o.fields())) < 1e-10
+    # steady: the inner and outer walls carry the same heat (energy balance)
+    assert dg["nu_i"] == pytest.approx(dg["nu_o"], rel=1e-3)
