@@ -204,9 +204,7 @@ LB_EXPORT lb_status lb_get_step(const lb_ctx *ctx, int64_t *step);
  * block (0 = automatic, at most 8) and how the FP32 / 16-bit step fetches
  * its rows (0 = automatic, 1 = plain loads, 2 = TMA bulk tensor copies into
  * a shared-memory ring, 3 = the same ring holding rows i - 1, i, i + 1 of
- * the step, read in place, 4 = the same on a persistent grid whose warps
- * fetch the next work item's rows while finishing the current one).
- * Results do not depend on the launch shape.
+ * the step, read in place).  Results do not depend on the launch shape.
  * LB_ERR_ARG for values out of range. */
 LB_EXPORT lb_status lb_set_launch(lb_ctx *ctx, int32_t seg_rows, int32_t warps_per_block, int32_t row_fetch);
 

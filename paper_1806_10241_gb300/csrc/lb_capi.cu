@@ -535,8 +535,8 @@ lb_status lb_get_step(const lb_ctx *ctx, int64_t *step)
 lb_status lb_set_launch(lb_ctx *ctx, int32_t seg_rows, int32_t warps_per_block, int32_t row_fetch)
 {
     if (!ctx) return fail(nullptr, LB_ERR_ARG, "ctx is NULL");
-    if (seg_rows < 0 || warps_per_block < 0 || warps_per_block > 8 || row_fetch < 0 || row_fetch > 4)
-        return fail(ctx, LB_ERR_ARG, "seg_rows >= 0, 0 <= warps_per_block <= 8, 0 <= row_fetch <= 4");
+    if (seg_rows < 0 || warps_per_block < 0 || warps_per_block > 8 || row_fetch < 0 || row_fetch > 3)
+        return fail(ctx, LB_ERR_ARG, "seg_rows >= 0, 0 <= warps_per_block <= 8, 0 <= row_fetch <= 3");
     if (seg_rows && (ctx->hp.nz + seg_rows - 1) / seg_rows > 65535)
         return fail(ctx, LB_ERR_ARG, "seg_rows too small for nz (more than 65535 segments)");
     Launch d = lbk::default_launch(ctx->hp);

@@ -770,7 +770,7 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG)
     rs.lane = threadIdx.x & 31;
     rs.status = status;
     rs.start();
-    march3<S>(k, src, dst, warp * 64, s, e, salt, rs);
+    march3<S, R>(k, src, dst, warp * 64, s, e, salt, rs);
 }
 
 // Stream function of the meridian flow (Sec. 3.6): dPsi/dy = -y u_x with
@@ -805,55 +805,6 @@ __global__ void __launch_bounds__(128) k_psi(const double *__restrict__ ux, doub
 }
 
 constexpr int kFieldRows = 32;  // rows per z-segment of the field export
-
-// The resident-row step on a persistent grid: each warp marches the work
-// items gw, gw + W, gw + 2W, ... (item = segment * nwin2 + window, W warps in
-// the grid) through one RowStream, so the first rows of an item are fetched
-// while the previous item finishes.
-template <typename S>
-__global__ void __maxnreg__(LB_STEP3_MAXREG)
-    k_step3p(KP<float> k, const __grid_constant__ CUtensorMap map, const S *__restrict__ src, S *__restrict__ dst,
-             int seg_rows, int nwin2, int nitems, uint32_t salt, int *status)
-{
-    constexpr int R = kRingStages<S>;
-    using Item = typename RowStream<S, R>::Item;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    const int gw = blockIdx.x * wpb + wib, W = gridDim.x * wpb;
-    if (gw >= nitems) return;
-    const int per_warp = R * TmaGeom<S>::stage_bytes + 128;
-    unsigned char *ring = smem + per_warp * wib;
-    auto item_of = [&](int it) {
-        Item r{0, 0, 0};
-        if (it < nitems) {
-            const int sg = it / nwin2, w = it - sg * nwin2;
-            const int s = sg * seg_rows, e = min(k.nz, s + seg_rows);
-            const bool has_m = s > 0 || k.xper, has_last = e < k.nz || k.xper;
-            r.first = has_m ? s - 1 : s;
-            r.nrows = (e - s) + (has_m ? 1 : 0) + (has_last ? 1 : 0);
-            r.x0 = w * 64 - TmaGeom<S>::off;
-        }
-        return r;
-    };
-    RowStream<S, R> rs;
-    rs.map = &map;
-    rs.ring = ring;
-    rs.ring_s = smem_u32(ring);
-    rs.bar_s = smem_u32(ring + R * TmaGeom<S>::stage_bytes);
-    rs.nz = k.nz;
-    rs.lane = threadIdx.x & 31;
-    rs.status = status;
-    rs.cur = item_of(gw);
-    rs.nxt = item_of(gw + W);
-    rs.start();
-    for (int it = gw; it < nitems; it += W) {
-        const int sg = it / nwin2, w = it - sg * nwin2;
-        const int s = sg * seg_rows, e = min(k.nz, s + seg_rows);
-        march3<S>(k, src, dst, w * 64, s, e, salt, rs);
-        if (rs.failed) return;
-        rs.next_item(item_of(it + 2 * W));
-    }
-}
 
 template <typename S, typename C>
 __global__ void __launch_bounds__(256) k_fields(KP<C> k, const S *__restrict__ src, double *__restrict__ out,
@@ -1259,7 +1210,7 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restric
         rs.lane = lane;
         rs.status = bd->status;
         rs.start();
-        march3<S>(k, (const S *)bd->buf[cur], (S *)bd->buf[cur ^ 1], w * 64, s, e, salt_of(bd->step0 + t), rs);
+        march3<S, R>(k, (const S *)bd->buf[cur], (S *)bd->buf[cur ^ 1], w * 64, s, e, salt_of(bd->step0 + t), rs);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1315,35 +1266,7 @@ cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *
     } else {
         const int nwin2 = nwindows2(h.nr);
         dim3 grid((nwin2 + wpb - 1) / wpb, (h.nz + seg - 1) / seg);
-        if (tmap && l.use_tma == 3) {
-            const size_t sm = ring_smem_bytes<S>(wpb);
-            static bool attr_set = false;
-            static int resident[9] = {0};  // blocks per SM for 1..8 warps per block
-            static int sms = 0;
-            if (!attr_set) {
-                cudaError_t e = cudaFuncSetAttribute(k_step3p<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)ring_smem_bytes<S>(8));
-                if (e != cudaSuccess) return e;
-                attr_set = true;
-            }
-            if (!resident[wpb]) {
-                int per = 0;
-                cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step3p<S>, 32 * wpb, sm);
-                if (e != cudaSuccess) return e;
-                resident[wpb] = per > 0 ? per : 1;
-            }
-            if (!sms) {
-                int dev = 0;
-                cudaGetDevice(&dev);
-                cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-                if (e != cudaSuccess) return e;
-            }
-            const int nitems = nwin2 * ((h.nz + seg - 1) / seg);
-            const int need = (nitems + wpb - 1) / wpb;
-            const int blocks = std::min(need, resident[wpb] * sms);
-            k_step3p<S><<<blocks, 32 * wpb, sm, s>>>(k, *(const CUtensorMap *)tmap, (const S *)src, (S *)dst, seg,
-                                                      nwin2, nitems, step_salt(step), status);
-        } else if (tmap && l.use_tma == 2) {
+        if (tmap && l.use_tma == 2) {
             const size_t sm = ring_smem_bytes<S>(wpb);
             static bool attr_set = false;
             if (!attr_set) {

@@ -903,131 +903,6 @@ template <typename S, int R> struct RowRing {
     }
 };
 
-// The same ring for a warp that marches a sequence of work items (window,
-// z-segment): the copies run on across item boundaries, so the first rows of
-// the next item are in flight while the current one finishes.  Sequence
-// indices are global (one per row fetched since start()); march3 addresses
-// the rows of the current item relative to `base`.
-template <typename S, int R> struct RowStream {
-    static_assert(R >= 3, "rows i - 1, i and i + 1 must fit");
-    struct Item {
-        int first, nrows, x0;  // first row (may be -1 or wrap), rows, TMA x start
-    };
-    const CUtensorMap *map;
-    const unsigned char *ring;
-    uint32_t ring_s, bar_s;
-    int nz, lane;
-    int base, rel;      // global index of the current item's row 0; its rows released so far
-    int waited, issued;  // global
-    Item cur, nxt;       // nxt.nrows = 0: no next item
-    int *status;
-    bool failed;         // a wait timed out (status set)
-
-    __device__ __forceinline__ void issue_row(int g, int row, int x0)
-    {
-        row = row >= nz ? row - nz : (row < 0 ? row + nz : row);
-        const int st = g % R;
-        const uint32_t bar = bar_s + 8u * st, dst = ring_s + (uint32_t)(TmaGeom<S>::stage_bytes * st);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"((uint32_t)TmaGeom<S>::box_bytes)
-                     : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-            "[%5];" ::"r"(dst),
-            "l"((unsigned long long)map), "r"(x0), "r"(row), "r"(0), "r"(bar)
-            : "memory");
-    }
-
-    // issue while a stage is free and a row of the current or the next item
-    // is still to fetch (lane 0 issues, every lane keeps the count)
-    __device__ __forceinline__ void top_up()
-    {
-        while (issued - (base + rel) < R) {
-            const int u = issued - base;  // index in the current item, or beyond it
-            int row, x0;
-            if (u < cur.nrows) {
-                row = cur.first + u;
-                x0 = cur.x0;
-            } else if (u - cur.nrows < nxt.nrows) {
-                row = nxt.first + (u - cur.nrows);
-                x0 = nxt.x0;
-            } else {
-                break;
-            }
-            if (lane == 0) issue_row(issued, row, x0);
-            ++issued;
-        }
-    }
-
-    __device__ __forceinline__ void start()
-    {
-        base = rel = waited = issued = 0;
-        failed = false;
-        if (lane == 0) {
-            for (int s = 0; s < R; ++s)
-                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s + 8u * s) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-        top_up();
-        __syncwarp();
-    }
-
-    // the current item is done: release its remaining rows, the next item
-    // becomes current (its successor is set by the caller before top_up)
-    __device__ __forceinline__ void next_item(const Item &after)
-    {
-        __syncwarp();
-        if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        base += cur.nrows;
-        rel = 0;
-        cur = nxt;
-        nxt = after;
-        top_up();
-    }
-
-    __device__ __forceinline__ bool wait_one(int g)
-    {
-        return mbar_wait_bounded(bar_s + 8u * (g % R), (uint32_t)((g / R) & 1), kTmaWaitLimit);
-    }
-
-    __device__ __forceinline__ bool wait_upto(int t)
-    {
-        bool ok = true;
-        while (waited <= base + t) {
-            if (!wait_one(waited)) {
-                ok = false;
-                break;
-            }
-            ++waited;
-        }
-        if (!__all_sync(FULL, ok)) {
-            failed = true;
-            if (lane == 0) atomicExch(status, (int)LB_ERR_TIMEOUT);
-            return false;
-        }
-        return true;
-    }
-
-    __device__ __forceinline__ const S *stage(int t) const
-    {
-        return reinterpret_cast<const S *>(ring + TmaGeom<S>::stage_bytes * ((base + t) % R));
-    }
-
-    // every lane is done with rows up to t of the current item
-    __device__ __forceinline__ void release(int t)
-    {
-        __syncwarp();
-        if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        rel = t + 1;
-        top_up();
-    }
-
-    __device__ __forceinline__ void finish()
-    {
-        for (int g = waited; g < issued; ++g) (void)wait_one(g);
-    }
-};
-
 // stage reads: the pair (A, B), the pair shifted one column left (A - 1, A)
 // or right (B, B + 1), and one column (the halo lanes)
 template <typename S> struct StageRd {
@@ -1056,9 +931,9 @@ template <typename S> struct StageRd {
     }
 };
 
-template <typename S, typename RS>
+template <typename S, int R>
 __device__ __forceinline__ void march3(const KP<float> &k, const S *__restrict__ src, S *__restrict__ dst, int c0,
-                                       int row_s, int row_e, uint32_t salt, RS &rs)
+                                       int row_s, int row_e, uint32_t salt, RowRing<S, R> &rs)
 {
     const Lane2 L = lane2(k, c0);
     const int lane = L.lane, nz = k.nz;

@@ -107,7 +107,7 @@ def test_create_and_parameter_validation_without_device_work(lib):
         assert lib.lb_set_params(ctx, C.byref(_abi.make_params(bad))) == _abi.LB_ERR_ARG
         assert b"periodic" in lib.lb_last_error(ctx)
         assert lib.lb_set_launch(ctx, 16, 9, 0) == _abi.LB_ERR_ARG
-        assert lib.lb_set_launch(ctx, 16, 4, 5) == _abi.LB_ERR_ARG
+        assert lib.lb_set_launch(ctx, 16, 4, 4) == _abi.LB_ERR_ARG
         seg, wpb, fetch = C.c_int32(), C.c_int32(), C.c_int32()
         assert lib.lb_set_launch(ctx, 5, 2, 2) == _abi.LB_OK
         assert lib.lb_get_launch(ctx, C.byref(seg), C.byref(wpb), C.byref(fetch)) == _abi.LB_OK

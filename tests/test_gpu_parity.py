@@ -181,7 +181,7 @@ def test_launch_shape_does_not_change_results():
     st = random_state(params, seed=5)
     ref = None
     for launch in ((0, 0, 0), (1, 1, 1), (7, 2, 1), (70, 4, 2), (16, 8, 2), (1, 1, 3), (6, 1, 3), (70, 4, 3),
-                   (16, 8, 3), (1, 1, 4), (4, 1, 4), (5, 2, 4), (70, 4, 4)):
+                   (16, 8, 3)):
         got, _, _, _ = run_both(params, st, 4, "fp32", launch)
         if ref is None:
             ref = got
