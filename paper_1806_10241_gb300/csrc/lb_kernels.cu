@@ -19,6 +19,7 @@
 // ones; lanes 0 and 31 are halo columns.  HBM traffic is therefore 19 loads
 // and 19 stores per node update.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1252,6 +1253,22 @@ size_t tma_smem_bytes(int wpb)
     return (size_t)wpb * (kTmaStages * TmaGeom<S>::stage_bytes + 128);
 }
 
+// The dynamic shared-memory limit of a kernel is a per-device attribute:
+// set it once on every device that launches the kernel (devices 0..63;
+// beyond that it is set at every launch).
+template <typename K>
+cudaError_t smem_limit_once(K kernel, int bytes, std::atomic<unsigned long long> &done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ULL << dev : 0ULL;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
+
 template <typename S, typename C>
 cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *dst, unsigned long long step,
                    const void *tmap, int *status, cudaStream_t s)
@@ -1268,24 +1285,16 @@ cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *
         dim3 grid((nwin2 + wpb - 1) / wpb, (h.nz + seg - 1) / seg);
         if (tmap && l.use_tma == 2) {
             const size_t sm = ring_smem_bytes<S>(wpb);
-            static bool attr_set = false;
-            if (!attr_set) {
-                cudaError_t e = cudaFuncSetAttribute(k_step3_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)ring_smem_bytes<S>(8));
-                if (e != cudaSuccess) return e;
-                attr_set = true;
-            }
+            static std::atomic<unsigned long long> attr_set{0};
+            cudaError_t e = smem_limit_once(k_step3_tma<S>, (int)ring_smem_bytes<S>(8), attr_set);
+            if (e != cudaSuccess) return e;
             k_step3_tma<S><<<grid, 32 * wpb, sm, s>>>(k, *(const CUtensorMap *)tmap, (const S *)src, (S *)dst, seg,
                                                        nwin2, step_salt(step), status);
         } else if (tmap && l.use_tma) {
             const size_t sm = tma_smem_bytes<S>(wpb);
-            static bool attr_set = false;
-            if (!attr_set) {
-                cudaError_t e = cudaFuncSetAttribute(k_step2_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)tma_smem_bytes<S>(8));
-                if (e != cudaSuccess) return e;
-                attr_set = true;
-            }
+            static std::atomic<unsigned long long> attr_set{0};
+            cudaError_t e = smem_limit_once(k_step2_tma<S>, (int)tma_smem_bytes<S>(8), attr_set);
+            if (e != cudaSuccess) return e;
             k_step2_tma<S><<<grid, 32 * wpb, sm, s>>>(k, *(const CUtensorMap *)tmap, (const S *)src, (S *)dst, seg,
                                                        nwin2, step_salt(step), status);
         } else {
