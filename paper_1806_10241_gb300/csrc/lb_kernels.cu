@@ -1346,6 +1346,18 @@ size_t storage_bytes(int storage)
     }
 }
 
+// SMs of the current device (152 on GB300; also the answer without a device)
+static int sm_count()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms <= 0) {
+        cudaGetLastError();  // clear the error of a query without a device
+        return 152;
+    }
+    return sms;
+}
+
 Launch default_launch(const HostParams &p)
 {
     Launch l;
@@ -1357,8 +1369,9 @@ Launch default_launch(const HostParams &p)
     const int nwin = p.storage == ST_FP64 ? nwindows(p.nr) : nwindows2(p.nr);
     int seg = p.storage == ST_FP64 ? 32 : 4;
     const long long warps = (long long)nwin * ((p.nz + seg - 1) / seg);
-    if (warps < 152LL * 16) {
-        const long long segs = (152LL * 16 + nwin - 1) / nwin;
+    const long long want = 16LL * sm_count();  // about two waves of resident warps
+    if (warps < want) {
+        const long long segs = (want + nwin - 1) / nwin;
         seg = (int)((p.nz + segs - 1) / segs);
         if (seg < 4) seg = 4;
     }
