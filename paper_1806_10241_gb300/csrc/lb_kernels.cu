@@ -738,6 +738,18 @@ __global__ void __maxnreg__(LB_STEP2_MAXREG)
 #endif
 template <typename S> constexpr int kRingStages = 4;
 
+// Programmatic dependent launch (sm_90+): the kernels of consecutive steps
+// are launched with programmatic stream serialisation, so a step's blocks
+// may start while the previous step's last blocks run.  Each block first
+// allows the next launch to begin, then waits until every earlier grid of
+// the stream has completed and its writes are visible, before it reads or
+// writes any distribution.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void grid_dependency_trigger_and_wait()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <typename S>
 size_t ring_smem_bytes(int wpb)
 {
@@ -770,6 +782,9 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG)
     rs.x0 = warp * 64 - TmaGeom<S>::off;
     rs.lane = threadIdx.x & 31;
     rs.status = status;
+    // programmatic dependent launch: let the next step's blocks become
+    // resident now, and touch no distribution before the previous step is done
+    grid_dependency_trigger_and_wait();
     rs.start();
     march3<S, R>(k, src, dst, warp * 64, s, e, salt, rs);
 }
@@ -1169,6 +1184,7 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restric
     __shared__ KP<float> skp[8];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
+    grid_dependency_trigger_and_wait();  // the previous step (and its counter update) is complete
     const unsigned long long t = *(volatile unsigned long long *)&ctl->counter;
     const int item = blockIdx.x * wpb + wib;
     if (item < total) {
@@ -1269,6 +1285,21 @@ cudaError_t smem_limit_once(K kernel, int bytes, std::atomic<unsigned long long>
     return e;
 }
 
+// Launch configuration with programmatic stream serialisation (see
+// grid_dependency_trigger_and_wait)
+void pdl_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr, dim3 grid, dim3 block, size_t smem,
+                cudaStream_t s)
+{
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+}
+
 template <typename S, typename C>
 cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *dst, unsigned long long step,
                    const void *tmap, int *status, cudaStream_t s)
@@ -1288,8 +1319,12 @@ cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *
             static std::atomic<unsigned long long> attr_set{0};
             cudaError_t e = smem_limit_once(k_step3_tma<S>, (int)ring_smem_bytes<S>(8), attr_set);
             if (e != cudaSuccess) return e;
-            k_step3_tma<S><<<grid, 32 * wpb, sm, s>>>(k, *(const CUtensorMap *)tmap, (const S *)src, (S *)dst, seg,
-                                                       nwin2, step_salt(step), status);
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute pdl[1];
+            pdl_config(cfg, pdl, grid, dim3(32 * wpb), sm, s);
+            e = cudaLaunchKernelEx(&cfg, k_step3_tma<S>, k, *(const CUtensorMap *)tmap, (const S *)src, (S *)dst,
+                                   seg, nwin2, step_salt(step), status);
+            if (e != cudaSuccess) return e;
         } else if (tmap && l.use_tma) {
             const size_t sm = tma_smem_bytes<S>(wpb);
             static std::atomic<unsigned long long> attr_set{0};
@@ -1548,20 +1583,20 @@ cudaError_t launch_batch(int storage, int row_fetch, const void *desc, const int
     if (row_fetch == 3) {
         const BatchDesc *dd = (const BatchDesc *)desc;
         BatchCtl *cc = (BatchCtl *)ctl;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute pdl[1];
         switch (storage) {
             case ST_FP32:
-                k_batch3<float><<<need, 32 * wpb, ring_smem_bytes<float>(wpb), s>>>(dd, prefix, n, total, cc);
-                break;
+                pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), ring_smem_bytes<float>(wpb), s);
+                return cudaLaunchKernelEx(&cfg, k_batch3<float>, dd, prefix, n, total, cc);
             case ST_FP16:
-                k_batch3<__half><<<need, 32 * wpb, ring_smem_bytes<__half>(wpb), s>>>(dd, prefix, n, total, cc);
-                break;
+                pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), ring_smem_bytes<__half>(wpb), s);
+                return cudaLaunchKernelEx(&cfg, k_batch3<__half>, dd, prefix, n, total, cc);
             case ST_BF16:
-                k_batch3<__nv_bfloat16>
-                    <<<need, 32 * wpb, ring_smem_bytes<__nv_bfloat16>(wpb), s>>>(dd, prefix, n, total, cc);
-                break;
+                pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), ring_smem_bytes<__nv_bfloat16>(wpb), s);
+                return cudaLaunchKernelEx(&cfg, k_batch3<__nv_bfloat16>, dd, prefix, n, total, cc);
             default: return cudaErrorInvalidValue;
         }
-        return cudaGetLastError();
     }
     const int grid = blocks < need ? blocks : need;
     switch (storage) {
