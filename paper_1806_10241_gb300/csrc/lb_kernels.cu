@@ -652,6 +652,18 @@ __device__ __forceinline__ void march(const KP<C> &k, const S *__restrict__ src,
 
 #include "lb_pair.cuh"
 
+// Programmatic dependent launch (sm_90+): the kernels of consecutive steps
+// are launched with programmatic stream serialisation, so a step's blocks
+// may start while the previous step's last blocks run.  Each block first
+// allows the next launch to begin, then waits until every earlier grid of
+// the stream has completed and its writes are visible, before it reads or
+// writes any distribution.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void grid_dependency_trigger_and_wait()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <typename S, typename C>
 __device__ __forceinline__ void step_body(const KP<C> &k, const S *__restrict__ src, S *__restrict__ dst,
                                           int seg_rows, int nwin)
@@ -661,6 +673,7 @@ __device__ __forceinline__ void step_body(const KP<C> &k, const S *__restrict__ 
     const int c = warp * OUT_COLS - 1 + (threadIdx.x & 31);
     const int s = blockIdx.y * seg_rows;
     const int e = min(k.nz, s + seg_rows);
+    grid_dependency_trigger_and_wait();
     march<S, C, MODE_STEP>(k, src, dst, nullptr, 0, 0, c, s, e, nullptr);
 }
 
@@ -691,6 +704,7 @@ __global__ void __maxnreg__(LB_STEP2_MAXREG) k_step2(KP<float> k, const S *__res
     hcol = hcol < 0 ? 0 : (hcol >= k.nr ? k.nr - 1 : hcol);
     RowDirect<S> rs{src, &k, A <= Amax ? A : Amax, hcol, (s > 0 || k.xper) ? s - 1 : s, k.nz, 0,
                     lane == 0 || lane == 31};
+    grid_dependency_trigger_and_wait();
     march2<S>(k, src, dst, warp * 64, s, e, salt, rs);
 }
 
@@ -726,6 +740,7 @@ __global__ void __maxnreg__(LB_STEP2_MAXREG)
     rs.lane = lane;
     rs.x0 = warp * 64 - TmaGeom<S>::off;
     rs.status = status;
+    grid_dependency_trigger_and_wait();
     rs.start();
     march2<S>(k, src, dst, warp * 64, s, e, salt, rs);
 }
@@ -737,18 +752,6 @@ __global__ void __maxnreg__(LB_STEP2_MAXREG)
 #define LB_STEP3_MAXREG 168
 #endif
 template <typename S> constexpr int kRingStages = 4;
-
-// Programmatic dependent launch (sm_90+): the kernels of consecutive steps
-// are launched with programmatic stream serialisation, so a step's blocks
-// may start while the previous step's last blocks run.  Each block first
-// allows the next launch to begin, then waits until every earlier grid of
-// the stream has completed and its writes are visible, before it reads or
-// writes any distribution.  Without the launch attribute both are no-ops.
-__device__ __forceinline__ void grid_dependency_trigger_and_wait()
-{
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-}
 
 template <typename S>
 size_t ring_smem_bytes(int wpb)
@@ -1310,7 +1313,11 @@ cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *
     if constexpr (std::is_same<C, double>::value) {
         const int nwin = nwindows(h.nr);
         dim3 grid((nwin + wpb - 1) / wpb, (h.nz + seg - 1) / seg);
-        k_step64<S, C><<<grid, 32 * wpb, 0, s>>>(k, (const S *)src, (S *)dst, seg, nwin);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute pdl[1];
+        pdl_config(cfg, pdl, grid, dim3(32 * wpb), 0, s);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_step64<S, C>, k, (const S *)src, (S *)dst, seg, nwin);
+        if (e != cudaSuccess) return e;
     } else {
         const int nwin2 = nwindows2(h.nr);
         dim3 grid((nwin2 + wpb - 1) / wpb, (h.nz + seg - 1) / seg);
@@ -1330,10 +1337,19 @@ cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *
             static std::atomic<unsigned long long> attr_set{0};
             cudaError_t e = smem_limit_once(k_step2_tma<S>, (int)tma_smem_bytes<S>(8), attr_set);
             if (e != cudaSuccess) return e;
-            k_step2_tma<S><<<grid, 32 * wpb, sm, s>>>(k, *(const CUtensorMap *)tmap, (const S *)src, (S *)dst, seg,
-                                                       nwin2, step_salt(step), status);
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute pdl[1];
+            pdl_config(cfg, pdl, grid, dim3(32 * wpb), sm, s);
+            e = cudaLaunchKernelEx(&cfg, k_step2_tma<S>, k, *(const CUtensorMap *)tmap, (const S *)src, (S *)dst,
+                                   seg, nwin2, step_salt(step), status);
+            if (e != cudaSuccess) return e;
         } else {
-            k_step2<S><<<grid, 32 * wpb, 0, s>>>(k, (const S *)src, (S *)dst, seg, nwin2, step_salt(step));
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute pdl[1];
+            pdl_config(cfg, pdl, grid, dim3(32 * wpb), 0, s);
+            cudaError_t e = cudaLaunchKernelEx(&cfg, k_step2<S>, k, (const S *)src, (S *)dst, seg, nwin2,
+                                               step_salt(step));
+            if (e != cudaSuccess) return e;
         }
     }
     return cudaGetLastError();
