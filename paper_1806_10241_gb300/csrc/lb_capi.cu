@@ -195,7 +195,7 @@ lb_status lb_create(const lb_grid_desc *desc, void *dev_buf, size_t bytes, void 
     h.plane = (long long)plane;
     h.storage = desc->storage;
     h.r0 = desc->r_inner;
-    h.scale = desc->storage == LB_FP16 ? 1024.0 : 1.0;
+    h.scale = desc->storage == LB_FP16 ? lbk::kFp16Scale : 1.0;
     c->buf = (char *)dev_buf;
     c->bytes = bytes;
     c->dist_bytes = dist;

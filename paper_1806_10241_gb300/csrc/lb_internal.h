@@ -11,6 +11,10 @@ enum Mode { MODE_STEP = 0, MODE_FIELDS = 1, MODE_DIAG = 2, MODE_DIAG_STRIP = 3 }
 enum Storage { ST_FP64 = 0, ST_FP32 = 1, ST_BF16 = 2, ST_FP16 = 3 };
 
 constexpr int NQ = 19;        // 9 (f) + 5 (g) + 5 (h) planes
+// FP16 storage holds the deviations times 2^10 (away from the subnormal
+// range); kFp16InvScaleBits is 2^-10 as an FP16 bit pattern
+constexpr double kFp16Scale = 1024.0;
+constexpr unsigned short kFp16InvScaleBits = 0x1400;
 constexpr int NSUM = 12;      // diagnostic partial sums per block
 constexpr int MAX_DIAG_BLOCKS = 4096;
 

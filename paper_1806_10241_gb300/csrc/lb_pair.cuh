@@ -124,10 +124,16 @@ struct NodeOut2 {
     F2 f[9], g[5], h[5];
 };
 
+// The post-collision values come out multiplied by osc, a power of two (the
+// FP16 storage scale, else 1): osc is folded into the constants of the
+// post-collision moments and into the fused multiply-add that adds them to
+// the streamed values.  Scaling by a power of two commutes with every
+// rounding, so the results are exactly osc times the unscaled ones.
 __device__ __forceinline__ void update_node2(const KP<float> &k, F2 iy, const F2 fv[9], const F2 gv[5],
                                              const F2 hv[5], F2 dxuy, F2 dyux, F2 dyuy, F2 dyut, F2 dyT,
-                                             NodeOut2 &o)
+                                             float osc, NodeOut2 &o)
 {
+    const F2 OS = sp(osc);
     // output moments, Eq. 18, 35, 47 (deviation form)
     const F2 a57 = fv[5] - fv[7], a86 = fv[8] - fv[6];
     const F2 s57 = fv[5] + fv[7], s68 = fv[6] + fv[8];
@@ -183,12 +189,12 @@ __device__ __forceinline__ void update_node2(const KP<float> &k, F2 iy, const F2
     const F2 Kxx = k3 + Dxx, Kyy = k3 + Dyy;
     const F2 ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
     const F2 uu = ux2 + uy2, ud = ux2 - uy2;
-    const F2 p3 = (fma2(rd, sp(2.0f / 3.0f), r * uu) - (Dxx + Dyy)) * sp(k.om3 * (1.0f / 12.0f));
-    const F2 c4 = sp(k.om4 * 0.25f);
+    const F2 p3 = (fma2(rd, sp(2.0f / 3.0f), r * uu) - (Dxx + Dyy)) * sp(k.om3 * (1.0f / 12.0f) * osc);
+    const F2 c4 = sp(k.om4 * 0.25f * osc);
     const F2 p4 = ((r * ud) - (Dxx - Dyy)) * c4;
     const F2 p5 = ((r * uxy) - Dxy) * c4;
     const F2 q34p = fma2(p3, sp(3.0f), p4), q34m = fma2(p3, sp(3.0f), p4 * sp(-1.0f));
-    const F2 ch = sp(k.omhi * 0.25f);
+    const F2 ch = sp(k.omhi * 0.25f * osc);
     const F2 m2p5 = p5 * sp(-2.0f);
     const F2 m2Dxy = Dxy * sp(-2.0f);
     const F2 r2 = r + r;
@@ -216,25 +222,25 @@ __device__ __forceinline__ void update_node2(const KP<float> &k, F2 iy, const F2
     p8 = fma2(uy, p6 * sp(-2.0f), p8);
     p8 = fma2(ux, p7 * sp(-2.0f), p8);
     // source moments, Eq. 26
-    const F2 p0 = MA * sp(1.0f / 9.0f), p1 = Fx * sp(1.0f / 6.0f), p2 = Fy * sp(1.0f / 6.0f);
+    const F2 p0 = MA * sp((1.0f / 9.0f) * osc), p1 = Fx * sp((1.0f / 6.0f) * osc), p2 = Fy * sp((1.0f / 6.0f) * osc);
     // back-transform, Eq. 27, grouped
     {
         const F2 A0 = p0 - p3;
         const F2 E = A0 + p4, Fm = A0 - p4;
         const F2 t78m = p7 - p8, t78p = p7 + p8, t68m = p6 - p8, t68p = p6 + p8;
-        o.f[0] = fma2(p3 - p8, sp(-4.0f), fv[0] + p0);
-        o.f[1] = (fv[1] + E) + fma2(t78m, sp(2.0f), p1);
-        o.f[3] = (fv[3] + E) - fma2(t78p, sp(2.0f), p1);
-        o.f[2] = (fv[2] + Fm) + fma2(t68m, sp(2.0f), p2);
-        o.f[4] = (fv[4] + Fm) - fma2(t68p, sp(2.0f), p2);
+        o.f[0] = fma2(p3 - p8, sp(-4.0f), fma2(fv[0], OS, p0));
+        o.f[1] = fma2(fv[1], OS, E) + fma2(t78m, sp(2.0f), p1);
+        o.f[3] = fma2(fv[3], OS, E) - fma2(t78p, sp(2.0f), p1);
+        o.f[2] = fma2(fv[2], OS, Fm) + fma2(t68m, sp(2.0f), p2);
+        o.f[4] = fma2(fv[4], OS, Fm) - fma2(t68p, sp(2.0f), p2);
         const F2 B0 = fma2(p3, sp(2.0f), p0 + p8);
         const F2 u12 = p1 + p2, v12 = p1 - p2, s67 = p6 + p7, d67 = p6 - p7;
         const F2 C5 = B0 + p5, C6 = B0 - p5;
         const F2 us = u12 - s67, vd = v12 + d67;
-        o.f[5] = (fv[5] + C5) + us;
-        o.f[7] = (fv[7] + C5) - us;
-        o.f[6] = (fv[6] + C6) - vd;
-        o.f[8] = (fv[8] + C6) + vd;
+        o.f[5] = fma2(fv[5], OS, C5) + us;
+        o.f[7] = fma2(fv[7], OS, C5) - us;
+        o.f[6] = fma2(fv[6], OS, C6) - vd;
+        o.f[8] = fma2(fv[8], OS, C6) + vd;
     }
 
     // D2Q5 cascaded collisions, Eq. 34 / 49 (sign reading of the paper: -)
@@ -243,7 +249,7 @@ __device__ __forceinline__ void update_node2(const KP<float> &k, F2 iy, const F2
     {
         const F2 kxn = gv[3] - gv[1], kyn = gv[4] - gv[2];  // -kappa'_x, -kappa'_y
         const F2 kxx = gv[1] + gv[3], kyy = gv[2] + gv[4];
-        const F2 cg = sp(k.omg * 0.5f);
+        const F2 cg = sp(k.omg * 0.5f * osc);
         const F2 q1 = fma2(ps, ux, kxn) * cg;
         const F2 q2 = fma2(ps, uy, kyn) * cg;
         const F2 m = fma2(ux, kxn, uy * kyn);  // -(ux kx + uy ky)
@@ -252,18 +258,18 @@ __device__ __forceinline__ void update_node2(const KP<float> &k, F2 iy, const F2
         const F2 X4 = fma2(ps, coefd, fma2(mm, sp(-2.0f), (kxx - kyy) * sp(-1.0f)));
         const F2 q3 = fma2(X3, ch, fma2(ux, q1, uy * q2));
         const F2 q4 = fma2(X4, ch, fma2(ux, q1, uy * q2 * sp(-1.0f)));
-        const F2 q0 = Sps * sp(0.2f);
+        const F2 q0 = Sps * sp(0.2f * osc);
         const F2 Q = q0 + q3, Qp = Q + q4, Qm = Q - q4;
-        o.g[0] = fma2(q3, sp(-4.0f), gv[0] + q0);
-        o.g[1] = (gv[1] + Qp) + q1;
-        o.g[3] = (gv[3] + Qp) - q1;
-        o.g[2] = (gv[2] + Qm) + q2;
-        o.g[4] = (gv[4] + Qm) - q2;
+        o.g[0] = fma2(q3, sp(-4.0f), fma2(gv[0], OS, q0));
+        o.g[1] = fma2(gv[1], OS, Qp) + q1;
+        o.g[3] = fma2(gv[3], OS, Qp) - q1;
+        o.g[2] = fma2(gv[2], OS, Qm) + q2;
+        o.g[4] = fma2(gv[4], OS, Qm) - q2;
     }
     {
         const F2 kxn = hv[3] - hv[1], kyn = hv[4] - hv[2];
         const F2 Hxx = hv[1] + hv[3], Hyy = hv[2] + hv[4];
-        const F2 ct = sp(k.omh * 0.5f);
+        const F2 ct = sp(k.omh * 0.5f * osc);
         const F2 r1 = fma2(phi, ux, kxn) * ct;
         const F2 r2t = fma2(phi, uy, kyn) * ct;
         const F2 m = fma2(ux, kxn, uy * kyn);
@@ -274,13 +280,13 @@ __device__ __forceinline__ void update_node2(const KP<float> &k, F2 iy, const F2
         const F2 X4 = fma2(phi, coefd, fma2(mm, sp(-2.0f), (Hxx - Hyy) * sp(-1.0f)));
         const F2 r3 = fma2(X3, ch, fma2(ux, r1, uy * r2t));
         const F2 r4 = fma2(X4, ch, fma2(ux, r1, uy * r2t * sp(-1.0f)));
-        const F2 r0 = Sph * sp(0.2f);
+        const F2 r0 = Sph * sp(0.2f * osc);
         const F2 Q = r0 + r3, Qp = Q + r4, Qm = Q - r4;
-        o.h[0] = fma2(r3, sp(-4.0f), hv[0] + r0);
-        o.h[1] = (hv[1] + Qp) + r1;
-        o.h[3] = (hv[3] + Qp) - r1;
-        o.h[2] = (hv[2] + Qm) + r2t;
-        o.h[4] = (hv[4] + Qm) - r2t;
+        o.h[0] = fma2(r3, sp(-4.0f), fma2(hv[0], OS, r0));
+        o.h[1] = fma2(hv[1], OS, Qp) + r1;
+        o.h[3] = fma2(hv[3], OS, Qp) - r1;
+        o.h[2] = fma2(hv[2], OS, Qm) + r2t;
+        o.h[4] = fma2(hv[4], OS, Qm) - r2t;
     }
 }
 
@@ -700,28 +706,28 @@ __device__ __forceinline__ void row_tail(const KP<float> &k, const S *__restrict
     const F2 dyut = (Rut - Lut) * hf;
     const F2 dyT = (RT - LT) * hf;
 
+    // FP16 storage: the update returns the values already times the scale
     NodeOut2 o;
-    update_node2(k, iy, fv, gv, hv5, dxuy, dyux, dyuy, dyut, dyT, o);
+    update_node2(k, iy, fv, gv, hv5, dxuy, dyux, dyuy, dyut, dyT, Scaled<S>::value ? sc : 1.0f, o);
 
     if (outA) {
         S *p = dst + (long long)i * k.pitch + A;
         uint32_t w = 0;
         if (PairIO<S>::rounds) w = pcg_hash(((uint32_t)i * (uint32_t)k.pitch + (uint32_t)A) ^ salt) | 1u;
-        const F2 m = sp(Scaled<S>::value ? sc : 1.0f);
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             if (PairIO<S>::rounds) w = xorshift32(w);
-            PairIO<S>::st(p + q * k.plane, Scaled<S>::value ? o.f[q] * m : o.f[q], w);
+            PairIO<S>::st(p + q * k.plane, o.f[q], w);
         }
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             if (PairIO<S>::rounds) w = xorshift32(w);
-            PairIO<S>::st(p + (G0 + q) * k.plane, Scaled<S>::value ? o.g[q] * m : o.g[q], w);
+            PairIO<S>::st(p + (G0 + q) * k.plane, o.g[q], w);
         }
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             if (PairIO<S>::rounds) w = xorshift32(w);
-            PairIO<S>::st(p + (H0 + q) * k.plane, Scaled<S>::value ? o.h[q] * m : o.h[q], w);
+            PairIO<S>::st(p + (H0 + q) * k.plane, o.h[q], w);
         }
     }
 
@@ -903,31 +909,68 @@ template <typename S, int R> struct RowRing {
     }
 };
 
+// Stored values to FP32, times the inverse storage scale.  For FP16 one
+// mixed-precision FMA per value (fma.rn.f32.f16, sm_100+) converts and
+// scales at once: h * 2^-10 + (-0) is exact, so the result is bitwise that
+// of a conversion followed by a multiplication.
+template <typename S> struct LoadScaled {
+    static __device__ __forceinline__ F2 pair(const S *p, float is)
+    {
+        const F2 v = PairIO<S>::ld(p);
+        return Scaled<S>::value ? v * sp(is) : v;
+    }
+    static __device__ __forceinline__ float one(const S *p, float is)
+    {
+        const float v = Cvt<S, float>::ld(p);
+        return Scaled<S>::value ? v * is : v;
+    }
+};
+template <> struct LoadScaled<__half> {
+    static_assert(kFp16Scale == 1024.0 && kFp16InvScaleBits == 0x1400, "FP16 scale is 2^10");
+    static __device__ __forceinline__ F2 pair(const __half *p, float)
+    {
+        const uint32_t raw = *reinterpret_cast<const uint32_t *>(p);
+        float x, y;
+        asm("{\n\t.reg .f16 lo, hi, s;\n\tmov.b32 {lo, hi}, %2;\n\tmov.b16 s, %3;\n\t"
+            "fma.rn.f32.f16 %0, lo, s, %4;\n\tfma.rn.f32.f16 %1, hi, s, %4;\n\t}"
+            : "=f"(x), "=f"(y)
+            : "r"(raw), "h"(kFp16InvScaleBits), "f"(-0.0f));
+        return mk2(x, y);
+    }
+    static __device__ __forceinline__ float one(const __half *p, float)
+    {
+        const unsigned short raw = *reinterpret_cast<const unsigned short *>(p);
+        float x;
+        asm("{\n\t.reg .f16 s;\n\tmov.b16 s, %2;\n\tfma.rn.f32.f16 %0, %1, s, %3;\n\t}"
+            : "=f"(x)
+            : "h"(raw), "h"(kFp16InvScaleBits), "f"(-0.0f));
+        return x;
+    }
+};
+
 // stage reads: the pair (A, B), the pair shifted one column left (A - 1, A)
 // or right (B, B + 1), and one column (the halo lanes)
 template <typename S> struct StageRd {
     const S *b;
     int cA;  // column of A inside the stage
     float is;
-    __device__ __forceinline__ F2 scl(F2 v) const { return Scaled<S>::value ? v * sp(is) : v; }
     __device__ __forceinline__ F2 pair(int q) const
     {
-        return scl(PairIO<S>::ld(b + q * TmaGeom<S>::cols + cA));
+        return LoadScaled<S>::pair(b + q * TmaGeom<S>::cols + cA, is);
     }
     __device__ __forceinline__ F2 left(int q) const
     {
         const S *p = b + q * TmaGeom<S>::cols + cA;
-        return scl(mk2(Cvt<S, float>::ld(p - 1), Cvt<S, float>::ld(p)));
+        return mk2(LoadScaled<S>::one(p - 1, is), LoadScaled<S>::one(p, is));
     }
     __device__ __forceinline__ F2 right(int q) const
     {
         const S *p = b + q * TmaGeom<S>::cols + cA;
-        return scl(mk2(Cvt<S, float>::ld(p + 1), Cvt<S, float>::ld(p + 2)));
+        return mk2(LoadScaled<S>::one(p + 1, is), LoadScaled<S>::one(p + 2, is));
     }
     __device__ __forceinline__ float col(int q, int c) const
     {
-        const float v = Cvt<S, float>::ld(b + q * TmaGeom<S>::cols + c);
-        return Scaled<S>::value ? v * is : v;
+        return LoadScaled<S>::one(b + q * TmaGeom<S>::cols + c, is);
     }
 };
 
