@@ -741,13 +741,17 @@ lb_status lb_batch_step(lb_batch *b, int32_t nsteps)
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch stream order");
     }
     int32_t left = nsteps;
+    unsigned long long t = b->counter;  // batch step of the next launch
     const bool use_graph = b->graph_steps > 1 && b->stream != nullptr && left >= b->graph_steps;
     if (use_graph && !b->graph_valid) {
+        // launches j = 0 .. K - 1 take steps counter + j; the last node adds K
         cudaGraph_t g;
         cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-        for (int t = 0; e == cudaSuccess && t < b->graph_steps; ++t)
-            e = lbk::launch_batch(b->storage, b->row_fetch, b->d_desc, b->d_prefix, (int)b->ctxs.size(), b->total, b->d_ctl,
-                                  b->wpb, b->blocks, b->stream);
+        for (int j = 0; e == cudaSuccess && j < b->graph_steps; ++j)
+            e = lbk::launch_batch(b->storage, b->row_fetch, b->d_desc, b->d_prefix, (int)b->ctxs.size(), b->total,
+                                  b->d_ctl, b->wpb, b->blocks, (unsigned long long)j, 1, b->stream);
+        if (e == cudaSuccess)
+            e = lbk::launch_batch_counter(b->d_ctl, (unsigned long long)b->graph_steps, 1, b->stream);
         cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) {
@@ -757,14 +761,17 @@ lb_status lb_batch_step(lb_batch *b, int32_t nsteps)
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch graph");
         b->graph_valid = true;
     }
-    if (use_graph)
-        for (; left >= b->graph_steps; left -= b->graph_steps) {
-            cudaError_t e = cudaGraphLaunch(b->gexec, b->stream);
+    if (use_graph) {
+        cudaError_t e = lbk::launch_batch_counter(b->d_ctl, t, 0, b->stream);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch counter");
+        for (; left >= b->graph_steps; left -= b->graph_steps, t += (unsigned long long)b->graph_steps) {
+            e = cudaGraphLaunch(b->gexec, b->stream);
             if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch graph launch");
         }
-    for (; left > 0; --left) {
+    }
+    for (; left > 0; --left, ++t) {
         cudaError_t e = lbk::launch_batch(b->storage, b->row_fetch, b->d_desc, b->d_prefix, (int)b->ctxs.size(), b->total,
-                                          b->d_ctl, b->wpb, b->blocks, b->stream);
+                                          b->d_ctl, b->wpb, b->blocks, t, 0, b->stream);
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch launch");
     }
     b->counter += (unsigned long long)nsteps;

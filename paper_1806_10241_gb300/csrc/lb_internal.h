@@ -86,9 +86,13 @@ int batch_grid(int storage, int wpb);
 // Kernel attributes of the batched step; called before any stream capture.
 cudaError_t batch_prepare(int storage);
 // row_fetch: 1 plain loads (persistent grid of `blocks`), 3 TMA ring read in
-// place (one warp per work item).
+// place (one warp per work item).  The launch takes batch step t0, plus the
+// device counter in ctl when from_counter is set (launches inside a graph).
 cudaError_t launch_batch(int storage, int row_fetch, const void *desc, const int *prefix, int n, int total,
-                         void *ctl, int wpb, int blocks, cudaStream_t s);
+                         void *ctl, int wpb, int blocks, unsigned long long t0, int from_counter,
+                         cudaStream_t s);
+// The device counter of a batch: set to value, or advanced by it (add != 0).
+cudaError_t launch_batch_counter(void *ctl, unsigned long long value, int add, cudaStream_t s);
 // Message for lb_last_error(NULL) on this thread.
 void set_global_error(const char *msg);
 Launch default_launch(const HostParams &p);

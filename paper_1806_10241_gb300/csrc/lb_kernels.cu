@@ -754,7 +754,7 @@ __global__ void __maxnreg__(LB_STEP2_MAXREG)
 template <typename S> constexpr int kRingStages = 4;
 
 template <typename S>
-size_t ring_smem_bytes(int wpb)
+__host__ __device__ size_t ring_smem_bytes(int wpb)
 {
     return (size_t)wpb * (kRingStages<S> * TmaGeom<S>::stage_bytes + 128);
 }
@@ -779,6 +779,7 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG)
     rs.ring = ring;
     rs.ring_s = smem_u32(ring);
     rs.bar_s = smem_u32(ring + R * TmaGeom<S>::stage_bytes);
+    rs.bar_stride = 8;
     rs.first = has_m ? s - 1 : s;
     rs.nrows = (e - s) + (has_m ? 1 : 0) + (has_last ? 1 : 0);
     rs.nz = k.nz;
@@ -1114,31 +1115,57 @@ struct alignas(128) BatchDesc {
     int nwin2, seg_rows, pad;
 };
 
+// The batch's step counter in device memory: the step at the start of the
+// running CUDA graph replay.  A graph holds K launches that take steps
+// counter + 0 .. counter + K - 1 and then a one-thread launch that adds K, so
+// every replay is the same; launches outside a graph get their step as a
+// parameter.
 struct BatchCtl {
-    unsigned long long counter;  // steps the batch has taken
-    unsigned int ticket;         // blocks finished in the running launch
-    unsigned int pad;
+    unsigned long long counter;
+    unsigned long long pad;
 };
+
+__global__ void k_batch_counter(BatchCtl *ctl, unsigned long long value, int add)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) ctl->counter = add ? ctl->counter + value : value;
+}
+
+// Instance of a work item: the last m < n with prefix[m] <= item (prefix is
+// non-decreasing, prefix[0] = 0 <= item < prefix[n]).  Each round tests 32
+// evenly spaced candidates of the remaining span with one load per lane and
+// a ballot: one round for n <= 32, two for n <= 1024.
+__device__ __forceinline__ int batch_instance(const int *__restrict__ prefix, int n, int item, int lane)
+{
+    int lo = 0, span = n;
+    while (span > 1) {
+        const int step = (span + 31) >> 5;
+        const int m = lo + lane * step;
+        const bool le = m < lo + span && prefix[m] <= item;
+        const unsigned mask = __ballot_sync(FULL, le);  // bit 0 set: prefix[lo] <= item
+        const int nlo = lo + (31 - __clz(mask)) * step;
+        span = min(step, lo + span - nlo);
+        lo = nlo;
+    }
+    return lo;
+}
 
 // Work items (instance, 64-column window, z-segment) are numbered by a prefix
 // sum over the instances and dealt to the warps of a persistent grid.  The
-// last block to finish advances the step counter, so every launch is the same
-// and a CUDA graph of several launches can be replayed.
+// step is t0, plus the device counter when from_counter is set (inside a
+// graph), so that every replay of a graph is the same.  Dynamic shared
+// memory: one KP per warp.
 template <typename S>
 __global__ void __maxnreg__(LB_STEP2_MAXREG) k_batch(const BatchDesc *__restrict__ d, const int *__restrict__ prefix,
-                                                     int n, int total, BatchCtl *ctl)
+                                                     int n, int total, const BatchCtl *ctl, unsigned long long t0,
+                                                     int from_counter)
 {
-    __shared__ KP<float> skp[8];
+    extern __shared__ __align__(128) unsigned char smem[];
+    KP<float> *skp = reinterpret_cast<KP<float> *>(smem);
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
-    const unsigned long long t = *(volatile unsigned long long *)&ctl->counter;
+    const unsigned long long t = t0 + (from_counter ? *(volatile const unsigned long long *)&ctl->counter : 0ULL);
     for (int item = blockIdx.x * wpb + wib; item < total; item += gridDim.x * wpb) {
-        int lo = 0, hi = n;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (prefix[mid] <= item) lo = mid;
-            else hi = mid;
-        }
+        const int lo = batch_instance(prefix, n, item, lane);
         const BatchDesc *bd = d + lo;
         __syncwarp();
         {
@@ -1163,40 +1190,43 @@ __global__ void __maxnreg__(LB_STEP2_MAXREG) k_batch(const BatchDesc *__restrict
                         lane == 0 || lane == 31};
         march2<S>(k, src, dst, w * 64, s, e, salt_of(bd->step0 + t), rs);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned int tk = atomicAdd(&ctl->ticket, 1u);
-        if (tk == gridDim.x - 1) {
-            ctl->ticket = 0;
-            ctl->counter = t + 1;
-            __threadfence();
-        }
-    }
 }
 
 // The batched step with the rows read in place from the TMA ring (march3):
-// one warp per work item, tensor maps from the lattice's descriptor.  The
-// step counter is read by every block before the last block advances it.
+// one warp per work item, tensor maps from the lattice's descriptor; the
+// step as in k_batch.  Dynamic shared memory: the warps' rings (each a
+// multiple of 128 bytes), then one KP per warp.  Each stage's mbarrier sits in
+// the padding after the stage's box, which the copies never write, so that
+// ten FP32 warps still fit on an SM (22,272 bytes per warp).
+template <typename S>
+__host__ __device__ constexpr size_t batch3_ring_bytes()
+{
+    static_assert(TmaGeom<S>::stage_bytes - TmaGeom<S>::box_bytes >= 8 && TmaGeom<S>::box_bytes % 8 == 0,
+                  "room for the stage's mbarrier after its box");
+    return (size_t)kRingStages<S> * TmaGeom<S>::stage_bytes;
+}
+template <typename S>
+__host__ __device__ size_t batch3_smem_bytes(int wpb)
+{
+    return (size_t)wpb * (batch3_ring_bytes<S>() + sizeof(KP<float>));
+}
+
 template <typename S>
 __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restrict__ d, const int *__restrict__ prefix,
-                                                      int n, int total, BatchCtl *ctl)
+                                                      int n, int total, const BatchCtl *ctl, unsigned long long t0,
+                                                      int from_counter)
 {
     constexpr int R = kRingStages<S>;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ KP<float> skp[8];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
-    grid_dependency_trigger_and_wait();  // the previous step (and its counter update) is complete
-    const unsigned long long t = *(volatile unsigned long long *)&ctl->counter;
+    unsigned char *ring = smem + batch3_ring_bytes<S>() * wib;
+    KP<float> *skp = reinterpret_cast<KP<float> *>(smem + batch3_ring_bytes<S>() * wpb);
+    grid_dependency_trigger_and_wait();  // the previous step (or counter update) is complete
+    const unsigned long long t = t0 + (from_counter ? *(volatile const unsigned long long *)&ctl->counter : 0ULL);
     const int item = blockIdx.x * wpb + wib;
     if (item < total) {
-        int lo = 0, hi = n;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (prefix[mid] <= item) lo = mid;
-            else hi = mid;
-        }
+        const int lo = batch_instance(prefix, n, item, lane);
         const BatchDesc *bd = d + lo;
         {
             const uint32_t *s = reinterpret_cast<const uint32_t *>(&bd->k);
@@ -1212,8 +1242,6 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restric
         const int seg = bd->seg_rows;
         const int s = sg * seg, e = min(k.nz, s + seg);
         const bool has_m = s > 0 || k.xper, has_last = e < k.nz || k.xper;
-        const int per_warp = R * TmaGeom<S>::stage_bytes + 128;
-        unsigned char *ring = smem + per_warp * wib;
         const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(bd->map[cur]);
         if (lane == 0)
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((unsigned long long)map)
@@ -1222,7 +1250,8 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restric
         rs.map = map;
         rs.ring = ring;
         rs.ring_s = smem_u32(ring);
-        rs.bar_s = smem_u32(ring + R * TmaGeom<S>::stage_bytes);
+        rs.bar_s = smem_u32(ring + TmaGeom<S>::box_bytes);
+        rs.bar_stride = TmaGeom<S>::stage_bytes;
         rs.first = has_m ? s - 1 : s;
         rs.nrows = (e - s) + (has_m ? 1 : 0) + (has_last ? 1 : 0);
         rs.nz = k.nz;
@@ -1231,16 +1260,6 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restric
         rs.status = bd->status;
         rs.start();
         march3<S, R>(k, (const S *)bd->buf[cur], (S *)bd->buf[cur ^ 1], w * 64, s, e, salt_of(bd->step0 + t), rs);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned int tk = atomicAdd(&ctl->ticket, 1u);
-        if (tk == gridDim.x - 1) {
-            ctl->ticket = 0;
-            ctl->counter = t + 1;
-            __threadfence();
-        }
     }
 }
 
@@ -1566,13 +1585,13 @@ cudaError_t batch_prepare(int storage)
     switch (storage) {
         case ST_FP32:
             return cudaFuncSetAttribute(k_batch3<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)ring_smem_bytes<float>(8));
+                                        (int)batch3_smem_bytes<float>(8));
         case ST_FP16:
             return cudaFuncSetAttribute(k_batch3<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)ring_smem_bytes<__half>(8));
+                                        (int)batch3_smem_bytes<__half>(8));
         case ST_BF16:
             return cudaFuncSetAttribute(k_batch3<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)ring_smem_bytes<__nv_bfloat16>(8));
+                                        (int)batch3_smem_bytes<__nv_bfloat16>(8));
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1582,49 +1601,53 @@ int batch_grid(int storage, int wpb)
     int dev = 0, sms = 152, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t sm = (size_t)wpb * sizeof(KP<float>);
     switch (storage) {
-        case ST_FP32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<float>, 32 * wpb, 0); break;
-        case ST_FP16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<__half>, 32 * wpb, 0); break;
-        case ST_BF16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<__nv_bfloat16>, 32 * wpb, 0); break;
+        case ST_FP32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<float>, 32 * wpb, sm); break;
+        case ST_FP16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<__half>, 32 * wpb, sm); break;
+        case ST_BF16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<__nv_bfloat16>, 32 * wpb, sm); break;
         default: per = 1;
     }
     return sms * (per > 0 ? per : 1);
 }
 
+cudaError_t launch_batch_counter(void *ctl, unsigned long long value, int add, cudaStream_t s)
+{
+    k_batch_counter<<<1, 32, 0, s>>>((BatchCtl *)ctl, value, add);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch(int storage, int row_fetch, const void *desc, const int *prefix, int n, int total,
-                         void *ctl, int wpb, int blocks, cudaStream_t s)
+                         void *ctl, int wpb, int blocks, unsigned long long t0, int from_counter, cudaStream_t s)
 {
     const int need = (total + wpb - 1) / wpb;
     if (need < 1) return cudaSuccess;
+    const BatchDesc *dd = (const BatchDesc *)desc;
+    const BatchCtl *cc = (const BatchCtl *)ctl;
     if (row_fetch == 3) {
-        const BatchDesc *dd = (const BatchDesc *)desc;
-        BatchCtl *cc = (BatchCtl *)ctl;
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute pdl[1];
         switch (storage) {
             case ST_FP32:
-                pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), ring_smem_bytes<float>(wpb), s);
-                return cudaLaunchKernelEx(&cfg, k_batch3<float>, dd, prefix, n, total, cc);
+                pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), batch3_smem_bytes<float>(wpb), s);
+                return cudaLaunchKernelEx(&cfg, k_batch3<float>, dd, prefix, n, total, cc, t0, from_counter);
             case ST_FP16:
-                pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), ring_smem_bytes<__half>(wpb), s);
-                return cudaLaunchKernelEx(&cfg, k_batch3<__half>, dd, prefix, n, total, cc);
+                pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), batch3_smem_bytes<__half>(wpb), s);
+                return cudaLaunchKernelEx(&cfg, k_batch3<__half>, dd, prefix, n, total, cc, t0, from_counter);
             case ST_BF16:
-                pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), ring_smem_bytes<__nv_bfloat16>(wpb), s);
-                return cudaLaunchKernelEx(&cfg, k_batch3<__nv_bfloat16>, dd, prefix, n, total, cc);
+                pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), batch3_smem_bytes<__nv_bfloat16>(wpb), s);
+                return cudaLaunchKernelEx(&cfg, k_batch3<__nv_bfloat16>, dd, prefix, n, total, cc, t0,
+                                          from_counter);
             default: return cudaErrorInvalidValue;
         }
     }
     const int grid = blocks < need ? blocks : need;
+    const size_t sm = (size_t)wpb * sizeof(KP<float>);
     switch (storage) {
-        case ST_FP32:
-            k_batch<float><<<grid, 32 * wpb, 0, s>>>((const BatchDesc *)desc, prefix, n, total, (BatchCtl *)ctl);
-            break;
-        case ST_FP16:
-            k_batch<__half><<<grid, 32 * wpb, 0, s>>>((const BatchDesc *)desc, prefix, n, total, (BatchCtl *)ctl);
-            break;
+        case ST_FP32: k_batch<float><<<grid, 32 * wpb, sm, s>>>(dd, prefix, n, total, cc, t0, from_counter); break;
+        case ST_FP16: k_batch<__half><<<grid, 32 * wpb, sm, s>>>(dd, prefix, n, total, cc, t0, from_counter); break;
         case ST_BF16:
-            k_batch<__nv_bfloat16>
-                <<<grid, 32 * wpb, 0, s>>>((const BatchDesc *)desc, prefix, n, total, (BatchCtl *)ctl);
+            k_batch<__nv_bfloat16><<<grid, 32 * wpb, sm, s>>>(dd, prefix, n, total, cc, t0, from_counter);
             break;
         default: return cudaErrorInvalidValue;
     }

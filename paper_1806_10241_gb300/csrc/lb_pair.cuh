@@ -827,7 +827,8 @@ template <typename S, int R> struct RowRing {
     static_assert(R >= 3, "rows i - 1, i and i + 1 must fit");
     const CUtensorMap *map;
     const unsigned char *ring;  // this warp's stages
-    uint32_t ring_s, bar_s;     // shared addresses of the stages and of the barriers
+    uint32_t ring_s, bar_s;     // shared addresses of the stages and of barrier 0
+    uint32_t bar_stride;        // bytes between consecutive barriers
     int first, nrows, nz, x0, lane, waited, issued;
     int *status;
 
@@ -836,7 +837,7 @@ template <typename S, int R> struct RowRing {
         int row = first + t;
         row = row >= nz ? row - nz : (row < 0 ? row + nz : row);
         const int st = t % R;
-        const uint32_t bar = bar_s + 8u * st, dst = ring_s + (uint32_t)(TmaGeom<S>::stage_bytes * st);
+        const uint32_t bar = bar_s + bar_stride * st, dst = ring_s + (uint32_t)(TmaGeom<S>::stage_bytes * st);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
                      "r"((uint32_t)TmaGeom<S>::box_bytes)
                      : "memory");
@@ -853,7 +854,7 @@ template <typename S, int R> struct RowRing {
         issued = nrows < R ? nrows : R;
         if (lane == 0) {
             for (int s = 0; s < R; ++s)
-                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s + 8u * s) : "memory");
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s + bar_stride * s) : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
             for (int t = 0; t < issued; ++t) issue(t);
         }
@@ -862,7 +863,7 @@ template <typename S, int R> struct RowRing {
 
     __device__ __forceinline__ bool wait_one(int t)
     {
-        return mbar_wait_bounded(bar_s + 8u * (t % R), (uint32_t)((t / R) & 1), kTmaWaitLimit);
+        return mbar_wait_bounded(bar_s + bar_stride * (t % R), (uint32_t)((t / R) & 1), kTmaWaitLimit);
     }
 
     // rows up to sequence index t have landed (false after a timeout, with

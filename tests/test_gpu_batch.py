@@ -54,7 +54,8 @@ def test_batch_equals_individual_runs(storage, row_fetch):
     b.set_launch(seg_rows=5, warps_per_block=4, graph_steps=4, row_fetch=1)  # plain loads, persistent grid
     b.step(16)  # 4 graph replays of 4 launches
     b.set_launch(seg_rows=3, warps_per_block=2, graph_steps=4, row_fetch=3)
-    b.step(16)
+    b.step(11)  # 2 graph replays, then 3 launches outside the graph
+    b.step(5)  # 1 replay, 1 launch
     torch.cuda.synchronize()
     for c, a, s in zip(cases, alone, mixed):
         assert s.step_count == 37
