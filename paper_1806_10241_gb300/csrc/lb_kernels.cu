@@ -752,6 +752,14 @@ __global__ void __maxnreg__(LB_STEP2_MAXREG)
 #define LB_STEP3_MAXREG 168
 #endif
 template <typename S> constexpr int kRingStages = 4;
+// march3 forms, as measured on GB300 (all give the same bits): the
+// single-lattice FP32 step takes the separate interior form of the row update
+// (+5 %; in 16-bit storage it cost 2-3 %) and every kernel reads the wall and
+// axis values from the ring, except the batched FP32 step, whose warps on
+// small lattices nearly all hold a wall or the axis and ran 6 % faster with
+// the values from global memory.
+template <typename S> constexpr bool kStepSplit = sizeof(S) == 4;
+template <typename S> constexpr bool kBatchOwnStage = sizeof(S) != 4;
 
 template <typename S>
 __host__ __device__ size_t ring_smem_bytes(int wpb)
@@ -790,7 +798,7 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG)
     // resident now, and touch no distribution before the previous step is done
     grid_dependency_trigger_and_wait();
     rs.start();
-    march3<S, R>(k, src, dst, warp * 64, s, e, salt, rs);
+    march3<S, R, kStepSplit<S>, true>(k, src, dst, warp * 64, s, e, salt, rs);
 }
 
 // Stream function of the meridian flow (Sec. 3.6): dPsi/dy = -y u_x with
@@ -1259,7 +1267,8 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restric
         rs.lane = lane;
         rs.status = bd->status;
         rs.start();
-        march3<S, R>(k, (const S *)bd->buf[cur], (S *)bd->buf[cur ^ 1], w * 64, s, e, salt_of(bd->step0 + t), rs);
+        march3<S, R, false, kBatchOwnStage<S>>(k, (const S *)bd->buf[cur], (S *)bd->buf[cur ^ 1], w * 64, s, e,
+                                               salt_of(bd->step0 + t), rs);
     }
 }
 

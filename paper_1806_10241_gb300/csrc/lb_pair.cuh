@@ -118,6 +118,45 @@ template <> struct PairIO<__nv_bfloat16> {
     }
 };
 
+// Stored values to FP32, times the inverse storage scale.  For FP16 one
+// mixed-precision FMA per value (fma.rn.f32.f16, sm_100+) converts and
+// scales at once: h * 2^-10 + (-0) is exact, so the result is bitwise that
+// of a conversion followed by a multiplication.
+template <typename S> struct LoadScaled {
+    static __device__ __forceinline__ F2 pair(const S *p, float is)
+    {
+        const F2 v = PairIO<S>::ld(p);
+        return Scaled<S>::value ? v * sp(is) : v;
+    }
+    static __device__ __forceinline__ float one(const S *p, float is)
+    {
+        const float v = Cvt<S, float>::ld(p);
+        return Scaled<S>::value ? v * is : v;
+    }
+};
+template <> struct LoadScaled<__half> {
+    static_assert(kFp16Scale == 1024.0 && kFp16InvScaleBits == 0x1400, "FP16 scale is 2^10");
+    static __device__ __forceinline__ F2 pair(const __half *p, float)
+    {
+        const uint32_t raw = *reinterpret_cast<const uint32_t *>(p);
+        float x, y;
+        asm("{\n\t.reg .f16 lo, hi, s;\n\tmov.b32 {lo, hi}, %2;\n\tmov.b16 s, %3;\n\t"
+            "fma.rn.f32.f16 %0, lo, s, %4;\n\tfma.rn.f32.f16 %1, hi, s, %4;\n\t}"
+            : "=f"(x), "=f"(y)
+            : "r"(raw), "h"(kFp16InvScaleBits), "f"(-0.0f));
+        return mk2(x, y);
+    }
+    static __device__ __forceinline__ float one(const __half *p, float)
+    {
+        const unsigned short raw = *reinterpret_cast<const unsigned short *>(p);
+        float x;
+        asm("{\n\t.reg .f16 s;\n\tmov.b16 s, %2;\n\tfma.rn.f32.f16 %0, %1, s, %3;\n\t}"
+            : "=f"(x)
+            : "h"(raw), "h"(kFp16InvScaleBits), "f"(-0.0f));
+        return x;
+    }
+};
+
 // ---- the node update on pairs ------------------------------------------------
 
 struct NodeOut2 {
@@ -556,18 +595,45 @@ __device__ __forceinline__ void halo_fields(const KP<float> &k, const float h[NQ
     T = k.T0 + (h[14] + h[15] + h[16] + h[17] + h[18]);
 }
 
+// Own post-collision values that the wall and axis rules need (own(q): the
+// lane's pair on row i; own0(q): column 0 on row i; m8 / p7: f8 on row i - 1
+// and f7 on row i + 1 at column 0, for the axis mirror).  OwnGlobal reads them
+// from the source buffer; OwnStage from the TMA ring, where they already are,
+// so that a warp at a wall or the axis waits on no global load.
+template <typename S> struct OwnGlobal {
+    const S *src;
+    const KP<float> *k;
+    int i, Ac;
+    __device__ __forceinline__ F2 own(int q) const { return own2<S>(src, *k, q, i, Ac); }
+    __device__ __forceinline__ float own0(int q) const { return own2<S>(src, *k, q, i, 0).v.x; }
+    __device__ __forceinline__ float m8() const { return own2<S>(src, *k, 8, i > 0 ? i - 1 : k->nz - 1, 0).v.x; }
+    __device__ __forceinline__ float p7() const { return own2<S>(src, *k, 7, i + 1 < k->nz ? i + 1 : 0, 0).v.x; }
+};
+template <typename S> struct OwnStage {
+    const S *b;  // stage of row i
+    int cA;      // column of the lane's pair in the stage
+    float is, m8v, p7v;
+    __device__ __forceinline__ F2 own(int q) const { return LoadScaled<S>::pair(b + q * TmaGeom<S>::cols + cA, is); }
+    __device__ __forceinline__ float own0(int q) const { return LoadScaled<S>::one(b + q * TmaGeom<S>::cols + cA, is); }
+    __device__ __forceinline__ float m8() const { return m8v; }
+    __device__ __forceinline__ float p7() const { return p7v; }
+};
+
 // The rest of a row update once the pulled values of the pair are in fv, gv,
 // hv5: wall and axis rules (the own post-collision values they need are read
 // from src), central differences of the stored-state fields with ghosts, the
-// node update and the stores.
-template <typename S>
-__device__ __forceinline__ void row_tail(const KP<float> &k, const S *__restrict__ src, S *__restrict__ dst,
-                                         const Lane2 &L, int i, bool has_m, bool has_p, uint32_t salt, F2 fv[9],
+// node update and the stores.  kBc = false is the interior form, for a warp
+// with no wall or axis column on a row with both neighbour rows: the rules are
+// left out at compile time instead of being branched or predicated around.
+template <typename S, bool kBc, typename Own>
+__device__ __forceinline__ void row_tail(const KP<float> &k, const Own &own, S *__restrict__ dst,
+                                         const Lane2 &L, int i, bool has_m_, bool has_p_, uint32_t salt, F2 fv[9],
                                          F2 gv[5], F2 hv5[5], const PM2 &pm_cur, const PM2 &pm_n, F2 uy_prev,
                                          float pmh_ux, float pmh_uy, float pmh_ut, float pmh_T)
 {
     const int lane = L.lane, A = L.A, Ac = L.Ac, nz = k.nz;
-    const bool outA = L.outA, atA0 = L.atA0, atAN = L.atAN, atBN = L.atBN, edge_warp = L.edge_warp;
+    const bool has_m = kBc ? has_m_ : true, has_p = kBc ? has_p_ : true;
+    const bool outA = L.outA, atA0 = L.atA0, atAN = L.atAN, atBN = L.atBN, edge_warp = kBc && L.edge_warp;
     const F2 y2 = L.y2, iy = L.iy;
     const float sc = k.scale;
     // lateral boundaries: column 0 is always the x of a pair, column
@@ -577,24 +643,24 @@ __device__ __forceinline__ void row_tail(const KP<float> &k, const S *__restrict
         if (atA0) {
             const int sd = 2;
             if (k.flow[sd] == 1) {  // axis: mirror images
-                fv[2].v.x = own2<S>(src, k, 4, i, 0).v.x;
-                if (has_m) fv[5].v.x = own2<S>(src, k, 8, i > 0 ? i - 1 : nz - 1, 0).v.x;
-                if (has_p) fv[6].v.x = own2<S>(src, k, 7, i + 1 < nz ? i + 1 : 0, 0).v.x;
+                fv[2].v.x = own.own0(4);
+                if (has_m) fv[5].v.x = own.m8();
+                if (has_p) fv[6].v.x = own.p7();
             } else {
                 const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
-                fv[2].v.x = own2<S>(src, k, 4, i, 0).v.x + rw * (6.0f / 9.0f) * uy_w;
-                fv[5].v.x = own2<S>(src, k, 7, i, 0).v.x + rw * (6.0f / 36.0f) * (ux_w + uy_w);
-                fv[6].v.x = own2<S>(src, k, 8, i, 0).v.x + rw * (6.0f / 36.0f) * (-ux_w + uy_w);
+                fv[2].v.x = own.own0(4) + rw * (6.0f / 9.0f) * uy_w;
+                fv[5].v.x = own.own0(7) + rw * (6.0f / 36.0f) * (ux_w + uy_w);
+                fv[6].v.x = own.own0(8) + rw * (6.0f / 36.0f) * (-ux_w + uy_w);
             }
-            gv[2].v.x = scalar_bc<float>(k.swirl[sd], own2<S>(src, k, G0 + 4, i, 0).v.x,
+            gv[2].v.x = scalar_bc<float>(k.swirl[sd], own.own0(G0 + 4),
                                          wall_psi<float>(k, sd, y2.v.x), true);
-            hv5[2].v.x = scalar_bc<float>(k.heat[sd], own2<S>(src, k, H0 + 4, i, 0).v.x, k.Tw[sd] - k.T0, false);
+            hv5[2].v.x = scalar_bc<float>(k.heat[sd], own.own0(H0 + 4), k.Tw[sd] - k.T0, false);
         }
         if (atAN || atBN) {
             const int sd = 3;
             const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
-            const F2 o2 = own2<S>(src, k, 2, i, Ac), o5 = own2<S>(src, k, 5, i, Ac), o6 = own2<S>(src, k, 6, i, Ac);
-            const F2 og = own2<S>(src, k, G0 + 2, i, Ac), oh = own2<S>(src, k, H0 + 2, i, Ac);
+            const F2 o2 = own.own(2), o5 = own.own(5), o6 = own.own(6);
+            const F2 og = own.own(G0 + 2), oh = own.own(H0 + 2);
             const float a4 = k.rho0 * (6.0f / 9.0f) * (-uy_w);
             const float a7 = k.rho0 * (6.0f / 36.0f) * (-ux_w - uy_w);
             const float a8 = k.rho0 * (6.0f / 36.0f) * (ux_w - uy_w);
@@ -619,10 +685,10 @@ __device__ __forceinline__ void row_tail(const KP<float> &k, const S *__restrict
     if (!has_m) {
         const int sd = 0;
         const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
-        fv[1] = own2<S>(src, k, 3, i, Ac) + sp(k.rho0 * (6.0f / 9.0f) * ux_w);
-        fv[5] = own2<S>(src, k, 7, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (ux_w + uy_w));
-        fv[8] = own2<S>(src, k, 6, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (ux_w - uy_w));
-        const F2 og = own2<S>(src, k, G0 + 3, i, Ac), oh = own2<S>(src, k, H0 + 3, i, Ac);
+        fv[1] = own.own(3) + sp(k.rho0 * (6.0f / 9.0f) * ux_w);
+        fv[5] = own.own(7) + sp(k.rho0 * (6.0f / 36.0f) * (ux_w + uy_w));
+        fv[8] = own.own(6) + sp(k.rho0 * (6.0f / 36.0f) * (ux_w - uy_w));
+        const F2 og = own.own(G0 + 3), oh = own.own(H0 + 3);
         gv[1] = mk2(scalar_bc<float>(k.swirl[sd], og.v.x, wall_psi<float>(k, sd, y2.v.x), true),
                     scalar_bc<float>(k.swirl[sd], og.v.y, wall_psi<float>(k, sd, y2.v.y), true));
         hv5[1] = mk2(scalar_bc<float>(k.heat[sd], oh.v.x, k.Tw[sd] - k.T0, false),
@@ -631,10 +697,10 @@ __device__ __forceinline__ void row_tail(const KP<float> &k, const S *__restrict
     if (!has_p) {
         const int sd = 1;
         const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
-        fv[3] = own2<S>(src, k, 1, i, Ac) + sp(k.rho0 * (6.0f / 9.0f) * (-ux_w));
-        fv[6] = own2<S>(src, k, 8, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (-ux_w + uy_w));
-        fv[7] = own2<S>(src, k, 5, i, Ac) + sp(k.rho0 * (6.0f / 36.0f) * (-ux_w - uy_w));
-        const F2 og = own2<S>(src, k, G0 + 1, i, Ac), oh = own2<S>(src, k, H0 + 1, i, Ac);
+        fv[3] = own.own(1) + sp(k.rho0 * (6.0f / 9.0f) * (-ux_w));
+        fv[6] = own.own(8) + sp(k.rho0 * (6.0f / 36.0f) * (-ux_w + uy_w));
+        fv[7] = own.own(5) + sp(k.rho0 * (6.0f / 36.0f) * (-ux_w - uy_w));
+        const F2 og = own.own(G0 + 1), oh = own.own(H0 + 1);
         gv[3] = mk2(scalar_bc<float>(k.swirl[sd], og.v.x, wall_psi<float>(k, sd, y2.v.x), true),
                     scalar_bc<float>(k.swirl[sd], og.v.y, wall_psi<float>(k, sd, y2.v.y), true));
         hv5[3] = mk2(scalar_bc<float>(k.heat[sd], oh.v.x, k.Tw[sd] - k.T0, false),
@@ -793,7 +859,7 @@ __device__ __forceinline__ void march2(const KP<float> &k, const S *__restrict__
         hv5[0] = x0_cur[6]; hv5[2] = x0_cur[7]; hv5[4] = x0_cur[8];
         fv[3] = xp_n[0]; fv[6] = xp_n[1]; fv[7] = xp_n[2]; gv[3] = xp_n[3]; hv5[3] = xp_n[4];
 
-        row_tail<S>(k, src, dst, L, i, has_m, has_p, salt, fv, gv, hv5, pm_cur, pm_n, uy_prev, pmh_ux, pmh_uy,
+        row_tail<S, true>(k, OwnGlobal<S>{src, &k, i, L.Ac}, dst, L, i, has_m, has_p, salt, fv, gv, hv5, pm_cur, pm_n, uy_prev, pmh_ux, pmh_uy,
                     pmh_ut, pmh_T);
 
         // rotate the row window
@@ -910,45 +976,6 @@ template <typename S, int R> struct RowRing {
     }
 };
 
-// Stored values to FP32, times the inverse storage scale.  For FP16 one
-// mixed-precision FMA per value (fma.rn.f32.f16, sm_100+) converts and
-// scales at once: h * 2^-10 + (-0) is exact, so the result is bitwise that
-// of a conversion followed by a multiplication.
-template <typename S> struct LoadScaled {
-    static __device__ __forceinline__ F2 pair(const S *p, float is)
-    {
-        const F2 v = PairIO<S>::ld(p);
-        return Scaled<S>::value ? v * sp(is) : v;
-    }
-    static __device__ __forceinline__ float one(const S *p, float is)
-    {
-        const float v = Cvt<S, float>::ld(p);
-        return Scaled<S>::value ? v * is : v;
-    }
-};
-template <> struct LoadScaled<__half> {
-    static_assert(kFp16Scale == 1024.0 && kFp16InvScaleBits == 0x1400, "FP16 scale is 2^10");
-    static __device__ __forceinline__ F2 pair(const __half *p, float)
-    {
-        const uint32_t raw = *reinterpret_cast<const uint32_t *>(p);
-        float x, y;
-        asm("{\n\t.reg .f16 lo, hi, s;\n\tmov.b32 {lo, hi}, %2;\n\tmov.b16 s, %3;\n\t"
-            "fma.rn.f32.f16 %0, lo, s, %4;\n\tfma.rn.f32.f16 %1, hi, s, %4;\n\t}"
-            : "=f"(x), "=f"(y)
-            : "r"(raw), "h"(kFp16InvScaleBits), "f"(-0.0f));
-        return mk2(x, y);
-    }
-    static __device__ __forceinline__ float one(const __half *p, float)
-    {
-        const unsigned short raw = *reinterpret_cast<const unsigned short *>(p);
-        float x;
-        asm("{\n\t.reg .f16 s;\n\tmov.b16 s, %2;\n\tfma.rn.f32.f16 %0, %1, s, %3;\n\t}"
-            : "=f"(x)
-            : "h"(raw), "h"(kFp16InvScaleBits), "f"(-0.0f));
-        return x;
-    }
-};
-
 // stage reads: the pair (A, B), the pair shifted one column left (A - 1, A)
 // or right (B, B + 1), and one column (the halo lanes)
 template <typename S> struct StageRd {
@@ -975,7 +1002,10 @@ template <typename S> struct StageRd {
     }
 };
 
-template <typename S, int R>
+// kSplit: interior rows of warps without wall or axis columns take the
+// interior form of row_tail.  kOwnStage: the wall and axis rules read the own
+// values from the ring (else from src).
+template <typename S, int R, bool kSplit, bool kOwnStage>
 __device__ __forceinline__ void march3(const KP<float> &k, const S *__restrict__ src, S *__restrict__ dst, int c0,
                                        int row_s, int row_e, uint32_t salt, RowRing<S, R> &rs)
 {
@@ -1017,6 +1047,7 @@ __device__ __forceinline__ void march3(const KP<float> &k, const S *__restrict__
         if (has_p && !rs.wait_upto(t + 1)) return rs.finish();
 
         F2 fv[9], gv[5], hv5[5];
+        OwnStage<S> own{rs.stage(t), O + 2 * lane, k.inv_scale, 0.0f, 0.0f};
         // e_x = +1 group from row i - 1, then that row's stage is free
         if (has_m) {
             rd.b = rs.stage(t - 1);
@@ -1025,6 +1056,7 @@ __device__ __forceinline__ void march3(const KP<float> &k, const S *__restrict__
             fv[8] = rd.right(8);
             gv[1] = rd.pair(G0 + 1);
             hv5[1] = rd.pair(H0 + 1);
+            if (kOwnStage && L.edge_warp) own.m8v = rd.pair(8).v.x;  // f8 of row i - 1, the lane's column
             rs.release(t - 1);
         } else {
             fv[1] = fv[5] = fv[8] = gv[1] = hv5[1] = sp(0.0f);
@@ -1059,13 +1091,21 @@ __device__ __forceinline__ void march3(const KP<float> &k, const S *__restrict__
             fv[7] = rd.right(7);
             gv[3] = v[G0 + 3];
             hv5[3] = v[H0 + 3];
+            own.p7v = v[7].v.x;  // f7 of row i + 1 at the lane's column (axis mirror)
         } else {
             fv[3] = fv[6] = fv[7] = gv[3] = hv5[3] = sp(0.0f);
             pm_n = pm_cur;
         }
 
-        row_tail<S>(k, src, dst, L, i, has_m, has_p, salt, fv, gv, hv5, pm_cur, pm_n, uy_prev, pmh_ux, pmh_uy,
-                    pmh_ut, pmh_T);
+        if (kSplit && has_m && has_p && !L.edge_warp)
+            row_tail<S, false>(k, own, dst, L, i, has_m, has_p, salt, fv, gv, hv5, pm_cur, pm_n, uy_prev, pmh_ux,
+                               pmh_uy, pmh_ut, pmh_T);
+        else if (kOwnStage)
+            row_tail<S, true>(k, own, dst, L, i, has_m, has_p, salt, fv, gv, hv5, pm_cur, pm_n, uy_prev, pmh_ux,
+                              pmh_uy, pmh_ut, pmh_T);
+        else
+            row_tail<S, true>(k, OwnGlobal<S>{src, &k, i, L.Ac}, dst, L, i, has_m, has_p, salt, fv, gv, hv5, pm_cur,
+                              pm_n, uy_prev, pmh_ux, pmh_uy, pmh_ut, pmh_T);
 
         uy_prev = pm_cur.uy;
         pm_cur = pm_n;
