@@ -104,3 +104,33 @@ def test_batch_diagnostics_equal_per_lattice_diagnostics():
     for t, a in zip(together, alone):
         assert t == a
     b.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_batch_of_many_lattices_equals_individual_runs(storage):
+    """70 small lattices: the instance lookup takes two rounds of its ballot
+    search (more than 32 instances), and a step count that is not a multiple
+    of the graph length mixes graph replays with single launches.  Every
+    lattice ends bitwise as it does alone."""
+    from paper_1806_10241_gb300.batch import Batch
+    from paper_1806_10241_gb300.solver import Solver
+    stream = torch.cuda.Stream()
+    cases = W.batched_instances(count=70, lo=8, hi=70)
+    alone = []
+    for c in cases:
+        s = Solver(c.params, storage=storage, stream=stream)
+        s.init_fields(c.fields)
+        s.step(23)
+        alone.append(s.get_dist())
+    mixed = []
+    for c in cases:
+        s = Solver(c.params, storage=storage, stream=stream)
+        s.init_fields(c.fields)
+        mixed.append(s)
+    b = Batch(mixed, stream=stream, graph_steps=10)
+    b.step(23)
+    torch.cuda.synchronize()
+    for c, a, s in zip(cases, alone, mixed):
+        assert s.step_count == 23
+        assert np.array_equal(s.get_dist(), a), c.name
+    b.close()
