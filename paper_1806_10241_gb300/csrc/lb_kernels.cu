@@ -1442,11 +1442,12 @@ Launch default_launch(const HostParams &p)
     Launch l;
     l.warps_per_block = p.storage == ST_FP64 ? 4 : 1;
     l.use_tma = p.storage != ST_FP64 ? 2 : 0;
-    // FP64: 32-row segments; pair kernels: 4-row segments (short segments
-    // balance the last wave; their halo rows are re-read from L2); fewer rows
-    // when the lattice would otherwise leave SMs idle
+    // FP64: 32-row segments; pair kernels: 4-row segments in FP32, 6 in
+    // 16-bit storage (measured on the 1024 x 2048 lattice; short segments
+    // balance the last wave, and their halo rows are re-read from L2); fewer
+    // rows when the lattice would otherwise leave SMs idle
     const int nwin = p.storage == ST_FP64 ? nwindows(p.nr) : nwindows2(p.nr);
-    int seg = p.storage == ST_FP64 ? 32 : 4;
+    int seg = p.storage == ST_FP64 ? 32 : (p.storage == ST_FP32 ? 4 : 6);
     const long long warps = (long long)nwin * ((p.nz + seg - 1) / seg);
     const long long want = 16LL * sm_count();  // about two waves of resident warps
     if (warps < want) {

@@ -123,7 +123,8 @@ def test_create_and_parameter_validation_without_device_work(lib):
 
 
 def test_default_launch_respects_the_grid_limit_for_tall_lattices(lib):
-    """4-row segments would need more than 65535 z-blocks for nz = 400000."""
+    """The default 6-row segments of 16-bit storage would need more than 65535
+    z-blocks for nz = 400000."""
     from paper_1806_10241_gb300 import _abi
     from paper_1806_10241_gb300 import workloads as W
     params = dict(W.swirling_cylinder(nr=64, nz=8).params, nz=400000)  # parameters only, no fields
