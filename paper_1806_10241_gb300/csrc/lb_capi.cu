@@ -587,6 +587,12 @@ struct lb_batch {
     std::vector<cudaStream_t> streams;   // the lattices' distinct streams other than the batch's
     std::vector<unsigned char> hdesc;
     std::vector<int> hprefix;
+    // batched diagnostics: per-lattice descriptors and block prefix sums
+    void *d_bdiag;
+    int *d_bprefix;
+    std::vector<unsigned char> hbdiag;
+    std::vector<int> hbprefix;
+    bool bdiag_uploaded;
 };
 
 // Work queued on the lattices' own streams (initialisation, state uploads,
@@ -605,16 +611,23 @@ static cudaError_t batch_streams_wait(lb_batch *b, bool batch_waits)
 
 constexpr size_t kDiagSlot = 256;  // per lattice: its NSUM sums and status word, gathered on the device
 
-static size_t batch_layout(int32_t n, size_t *desc_off, size_t *prefix_off, size_t *ctl_off, size_t *diag_off)
+// Batch buffer: descriptors, item prefix sums, step counter, gathered
+// diagnostics, diagnostics descriptors, diagnostics block prefix sums.
+static size_t batch_layout(int32_t n, size_t *desc_off, size_t *prefix_off, size_t *ctl_off, size_t *diag_off,
+                           size_t *bdiag_off = nullptr, size_t *bprefix_off = nullptr)
 {
     const size_t d = align256((size_t)n * lbk::batch_desc_bytes());
     const size_t p = align256((size_t)(n + 1) * sizeof(int));
     const size_t t = align256(lbk::batch_ctl_bytes());
+    const size_t g = align256((size_t)n * kDiagSlot);
+    const size_t bd = align256((size_t)n * lbk::batch_diag_bytes());
     *desc_off = 0;
     *prefix_off = d;
     *ctl_off = d + p;
     *diag_off = d + p + t;
-    return d + p + t + (size_t)n * kDiagSlot;
+    if (bdiag_off) *bdiag_off = d + p + t + g;
+    if (bprefix_off) *bprefix_off = d + p + t + g + bd;
+    return d + p + t + g + bd + (size_t)(n + 1) * sizeof(int);
 }
 
 static lb_status batch_upload(lb_batch *b)
@@ -657,8 +670,8 @@ lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_buf, size_t 
 {
     if (!out || !ctxs || n < 1 || !dev_buf) return fail(nullptr, LB_ERR_ARG, "NULL argument or n < 1");
     *out = nullptr;
-    size_t doff, poff, coff, goff;
-    const size_t need = batch_layout(n, &doff, &poff, &coff, &goff);
+    size_t doff, poff, coff, goff, bdoff, bpoff;
+    const size_t need = batch_layout(n, &doff, &poff, &coff, &goff, &bdoff, &bpoff);
     if (bytes < need) return fail(nullptr, LB_ERR_NOMEM, "batch buffer holds %zu bytes, %zu needed", bytes, need);
     if (((uintptr_t)dev_buf & 255) != 0) return fail(nullptr, LB_ERR_ARG, "dev_buf must be 256-byte aligned");
     const int storage = ctxs[0] ? ctxs[0]->hp.storage : -1;
@@ -684,6 +697,9 @@ lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_buf, size_t 
     b->d_ctl = b->buf + coff;
     b->d_diag = b->buf + goff;
     b->hdiag.assign((size_t)n * kDiagSlot, 0);
+    b->d_bdiag = b->buf + bdoff;
+    b->d_bprefix = (int *)(b->buf + bpoff);
+    b->bdiag_uploaded = false;
     b->stream = (cudaStream_t)cuda_stream;
     b->seg_rows = 4;
     b->wpb = 1;
@@ -789,15 +805,30 @@ lb_status lb_batch_diagnostics(lb_batch *b, lb_diag *out)
 {
     if (!b || !out) return fail(nullptr, LB_ERR_ARG, "batch or out is NULL");
     cudaError_t e = batch_streams_wait(b, true);
-    const size_t res_bytes = 128 + sizeof(int);  // NSUM sums, padding, status word
-    for (size_t m = 0; e == cudaSuccess && m < b->ctxs.size(); ++m) {
+    // each lattice's diagnostics grid as lb_diagnostics would launch it (its
+    // launch settings may have changed since the last call)
+    const int n = (int)b->ctxs.size();
+    const size_t gb = lbk::batch_diag_bytes();
+    std::vector<unsigned char> hd((size_t)n * gb);
+    std::vector<int> hp((size_t)n + 1, 0);
+    for (int m = 0; m < n; ++m) {
         lb_ctx *c = b->ctxs[m];
-        e = lbk::launch_diag(c->hp, diag_launch(c), c->dist[c->cur], c->partial, (double *)c->dist[1 - c->cur],
-                             c->result, b->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(b->d_diag + m * kDiagSlot, c->result, res_bytes, cudaMemcpyDeviceToDevice,
-                                b->stream);
+        const int nb = lbk::batch_fill_diag(c->hp, diag_launch(c), c->partial, hd.data() + (size_t)m * gb);
+        if (nb < 1) return fail(nullptr, LB_ERR_ARG, "lattice %d: diagnostics grid too large", m);
+        hp[m + 1] = hp[m] + nb;
     }
+    if (e == cudaSuccess && (!b->bdiag_uploaded || hd != b->hbdiag || hp != b->hbprefix)) {
+        b->hbdiag.swap(hd);
+        b->hbprefix.swap(hp);
+        e = cudaMemcpyAsync(b->d_bdiag, b->hbdiag.data(), b->hbdiag.size(), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_bprefix, b->hbprefix.data(), b->hbprefix.size() * sizeof(int),
+                                cudaMemcpyHostToDevice, b->stream);
+        b->bdiag_uploaded = e == cudaSuccess;
+    }
+    if (e == cudaSuccess)
+        e = lbk::launch_batch_diag(b->storage, b->d_desc, b->d_bdiag, b->d_bprefix, n, b->hbprefix[n], b->counter,
+                                   (double *)b->d_diag, (int)(kDiagSlot / sizeof(double)), b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->hdiag.data(), b->d_diag, b->hdiag.size(), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);

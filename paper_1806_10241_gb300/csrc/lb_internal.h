@@ -93,6 +93,15 @@ cudaError_t launch_batch(int storage, int row_fetch, const void *desc, const int
                          cudaStream_t s);
 // The device counter of a batch: set to value, or advanced by it (add != 0).
 cudaError_t launch_batch_counter(void *ctl, unsigned long long value, int add, cudaStream_t s);
+// Batched diagnostics: one descriptor per lattice (its partial-sum buffer and
+// the grid of its own diagnostics under launch l; returns the number of
+// blocks, -1 above MAX_DIAG_BLOCKS), block prefix sums over the lattices, and
+// the three launches that write each lattice's sums and status word into
+// out + m * slot_doubles after t batch steps.
+size_t batch_diag_bytes();
+int batch_fill_diag(const HostParams &h, const Launch &l, double *partial, void *out);
+cudaError_t launch_batch_diag(int storage, const void *desc, const void *bdiag, const int *bprefix, int n, int total,
+                              unsigned long long t, double *out, int slot_doubles, cudaStream_t s);
 // Message for lb_last_error(NULL) on this thread.
 void set_global_error(const char *msg);
 Launch default_launch(const HostParams &p);

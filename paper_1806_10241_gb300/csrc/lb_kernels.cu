@@ -861,17 +861,19 @@ __device__ __forceinline__ double warp_max(double v)
 // One warp per 30-column window, whole height (the end-wall fluxes need rows
 // 0, 1 and nz-2, nz-1 in the same march).  Block partial sums in a fixed
 // order, then a single-block final reduction: deterministic.
+// Block (bx, by) of a diagnostics grid gx blocks wide; 128 threads.
 template <typename S, typename C>
-__global__ void __launch_bounds__(128) k_diag(KP<C> k, const S *__restrict__ src, double *__restrict__ partial,
-                                              double *__restrict__ tfield, int seg_rows, int nwin)
+__device__ __forceinline__ void diag_block(const KP<C> &k, const S *__restrict__ src, double *__restrict__ partial,
+                                           double *__restrict__ tfield, int seg_rows, int nwin, int bx, int by,
+                                           int gx)
 {
     __shared__ double sh[4][NSUM];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+    const int warp = bx * (blockDim.x >> 5) + wib;
     DiagAcc a = {0, 0, 0, 0, 0};
     if (warp < nwin) {
         const int c = warp * OUT_COLS - 1 + lane;
-        const int s = blockIdx.y * seg_rows, e = min(k.nz, s + seg_rows);
+        const int s = by * seg_rows, e = min(k.nz, s + seg_rows);
         march<S, C, MODE_DIAG>(k, src, nullptr, tfield, 0, 0, c, s, e, &a);
     }
     double vals[NSUM] = {a.mass_dev, a.mass_r_dev, a.tsum, a.umax, 0, 0, 0, 0, a.bad, 0, 0, 0};
@@ -884,8 +886,15 @@ __global__ void __launch_bounds__(128) k_diag(KP<C> k, const S *__restrict__ src
         const int q = threadIdx.x;
         double r = sh[0][q];
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = (q == 3 || q == 8) ? fmax(r, sh[w][q]) : r + sh[w][q];
-        partial[(blockIdx.y * gridDim.x + blockIdx.x) * NSUM + q] = r;
+        partial[(by * gx + bx) * NSUM + q] = r;
     }
+}
+
+template <typename S, typename C>
+__global__ void __launch_bounds__(128) k_diag(KP<C> k, const S *__restrict__ src, double *__restrict__ partial,
+                                              double *__restrict__ tfield, int seg_rows, int nwin)
+{
+    diag_block<S, C>(k, src, partial, tfield, seg_rows, nwin, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 // Wall heat-flux sums (Sec. 3.2) from the pre-collision T field: one-sided
@@ -893,7 +902,7 @@ __global__ void __launch_bounds__(128) k_diag(KP<C> k, const S *__restrict__ src
 // (-8 T_w + 9 T_1 - T_2) / 3 along the inward direction; end walls weighted
 // by the radius.  One block, fixed-order tree reduction (deterministic).
 template <typename C>
-__global__ void __launch_bounds__(256) k_wall(KP<C> k, const double *__restrict__ T, double *__restrict__ result)
+__device__ __forceinline__ void wall_block(const KP<C> &k, const double *__restrict__ T, double *__restrict__ result)
 {
     __shared__ double sh[256];
     const int nr = k.nr, nz = k.nz;
@@ -924,6 +933,12 @@ __global__ void __launch_bounds__(256) k_wall(KP<C> k, const double *__restrict_
         if (threadIdx.x == 0) result[4 + sd] = k.heat[sd] == 0 ? sh[0] * k.nu_scale[sd] : 0.0;
         __syncthreads();
     }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_wall(KP<C> k, const double *__restrict__ T, double *__restrict__ result)
+{
+    wall_block<C>(k, T, result);
 }
 
 // Variant of k_diag whose temperature output is the wall-adjacent strips
@@ -993,8 +1008,8 @@ __global__ void __launch_bounds__(256) k_wall_strip(KP<C> k, const double *__res
 
 // One block of 256 threads: per sum, strided partial sums in a fixed order,
 // then a fixed tree (deterministic for a given number of blocks).
-__global__ void __launch_bounds__(256) k_diag_final(const double *__restrict__ partial, int nblocks,
-                                                    double *__restrict__ result)
+__device__ __forceinline__ void diag_final_block(const double *__restrict__ partial, int nblocks,
+                                                 double *__restrict__ result)
 {
     __shared__ double sh[256];
     for (int q = 0; q < NSUM; ++q) {
@@ -1015,6 +1030,12 @@ __global__ void __launch_bounds__(256) k_diag_final(const double *__restrict__ p
         if (threadIdx.x == 0) result[q] = sh[0];
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(256) k_diag_final(const double *__restrict__ partial, int nblocks,
+                                                    double *__restrict__ result)
+{
+    diag_final_block(partial, nblocks, result);
 }
 
 // ---- initialisation and exchange ---------------------------------------------
@@ -1270,6 +1291,58 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restric
         march3<S, R, false, kBatchOwnStage<S>>(k, (const S *)bd->buf[cur], (S *)bd->buf[cur ^ 1], w * 64, s, e,
                                                salt_of(bd->step0 + t), rs);
     }
+}
+
+// Diagnostics of every lattice of a batch in three launches instead of three
+// per lattice: the blocks of all the lattices' diagnostics grids in one grid,
+// then one final-reduction block and one wall-flux block per lattice.  Each
+// lattice keeps the grid and summation order of its own diagnostics, so the
+// results are bitwise those of lb_diagnostics.
+struct BatchDiag {
+    double *partial;         // the lattice's block partial sums
+    int gx, gy, seg, nwin;   // its diagnostics grid (diag_t)
+};
+
+template <typename S>
+__global__ void __launch_bounds__(128) k_batch_diag(const BatchDesc *__restrict__ d,
+                                                    const BatchDiag *__restrict__ dd, const int *__restrict__ prefix,
+                                                    int n, unsigned long long t)
+{
+    // the lattice of this block: the last m with prefix[m] <= blockIdx.x
+    const int blk = blockIdx.x;
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= blk) lo = mid;
+        else hi = mid;
+    }
+    const BatchDesc &bd = d[lo];
+    const BatchDiag &g = dd[lo];
+    const int local = blk - prefix[lo];
+    const int cur = (bd.parity0 + (int)(t & 1ULL)) & 1;  // the lattice's current buffer after t batch steps
+    diag_block<S, float>(bd.k, (const S *)bd.buf[cur], g.partial, (double *)bd.buf[cur ^ 1], g.seg, g.nwin,
+                         local % g.gx, local / g.gx, g.gx);
+}
+
+// out: one slot of slot_doubles per lattice, its NSUM sums and, 128 bytes in,
+// the lattice's status word
+__global__ void __launch_bounds__(256) k_batch_diag_final(const BatchDesc *__restrict__ d,
+                                                          const BatchDiag *__restrict__ dd, double *__restrict__ out,
+                                                          int slot_doubles)
+{
+    const int m = blockIdx.x;
+    double *res = out + (size_t)m * slot_doubles;
+    diag_final_block(dd[m].partial, dd[m].gx * dd[m].gy, res);
+    if (threadIdx.x == 0) *reinterpret_cast<int *>(res + 16) = *d[m].status;
+}
+
+__global__ void __launch_bounds__(256) k_batch_wall(const BatchDesc *__restrict__ d, double *__restrict__ out,
+                                                    int slot_doubles, unsigned long long t)
+{
+    const int m = blockIdx.x;
+    const BatchDesc &bd = d[m];
+    const int cur = (bd.parity0 + (int)(t & 1ULL)) & 1;
+    wall_block<float>(bd.k, (const double *)bd.buf[cur ^ 1], out + (size_t)m * slot_doubles);
 }
 
 // Self-test of the bounded waits: one warp waits on an mbarrier that nothing
@@ -1661,6 +1734,37 @@ cudaError_t launch_batch(int storage, int row_fetch, const void *desc, const int
             break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+size_t batch_diag_bytes() { return sizeof(BatchDiag); }
+
+int batch_fill_diag(const HostParams &h, const Launch &l, double *partial, void *out)
+{
+    BatchDiag g;
+    g.partial = partial;
+    g.nwin = nwindows(h.nr);
+    g.seg = l.seg_rows;
+    g.gx = (g.nwin + 3) / 4;
+    g.gy = (h.nz + g.seg - 1) / g.seg;
+    std::memcpy(out, &g, sizeof g);
+    const int nb = g.gx * g.gy;
+    return nb <= MAX_DIAG_BLOCKS ? nb : -1;
+}
+
+cudaError_t launch_batch_diag(int storage, const void *desc, const void *bdiag, const int *bprefix, int n, int total,
+                              unsigned long long t, double *out, int slot_doubles, cudaStream_t s)
+{
+    const BatchDesc *d = (const BatchDesc *)desc;
+    const BatchDiag *dd = (const BatchDiag *)bdiag;
+    switch (storage) {
+        case ST_FP32: k_batch_diag<float><<<total, 128, 0, s>>>(d, dd, bprefix, n, t); break;
+        case ST_FP16: k_batch_diag<__half><<<total, 128, 0, s>>>(d, dd, bprefix, n, t); break;
+        case ST_BF16: k_batch_diag<__nv_bfloat16><<<total, 128, 0, s>>>(d, dd, bprefix, n, t); break;
+        default: return cudaErrorInvalidValue;
+    }
+    k_batch_diag_final<<<n, 256, 0, s>>>(d, dd, out, slot_doubles);
+    k_batch_wall<<<n, 256, 0, s>>>(d, out, slot_doubles, t);
     return cudaGetLastError();
 }
 
