@@ -134,3 +134,23 @@ def test_batch_of_many_lattices_equals_individual_runs(storage):
         assert s.step_count == 23
         assert np.array_equal(s.get_dist(), a), c.name
     b.close()
+
+
+def test_batch_diagnostics_follow_a_changed_launch():
+    """A lattice whose launch settings change between two calls gets the
+    diagnostics grid of its new settings: still bitwise its own diagnostics."""
+    from paper_1806_10241_gb300.batch import Batch
+    from paper_1806_10241_gb300.solver import Solver
+    stream = torch.cuda.Stream()
+    sols = []
+    for c in _cases()[:5]:
+        s = Solver(c.params, storage="fp32", stream=stream)
+        s.init_fields(c.fields)
+        sols.append(s)
+    b = Batch(sols, stream=stream, graph_steps=5)
+    b.step(12)
+    assert b.diag() == [s.diag() for s in sols]
+    sols[2].set_launch(48, 2, 0)  # 48-row segments: another diagnostics grid
+    b.step(3)
+    assert b.diag() == [s.diag() for s in sols]
+    b.close()
