@@ -263,8 +263,10 @@ LB_EXPORT lb_status lb_batch_set_launch(lb_batch *b, int32_t seg_rows, int32_t w
                                         int32_t graph_steps, int32_t row_fetch);
 LB_EXPORT lb_status lb_batch_step(lb_batch *b, int32_t nsteps);
 /* lb_diagnostics of every lattice of the batch (out[n], in the order of
- * lb_batch_create): the reductions of all lattices are queued on the batch
- * stream and read back with one copy; synchronises the batch stream. */
+ * lb_batch_create), bitwise equal to lb_diagnostics of each lattice: three
+ * launches on the batch stream for all lattices (each lattice's reduction
+ * grid and order as lb_diagnostics uses them), one copy back; synchronises
+ * the batch stream. */
 LB_EXPORT lb_status lb_batch_diagnostics(lb_batch *b, lb_diag *out);
 LB_EXPORT lb_status lb_batch_destroy(lb_batch *b);
 
