@@ -30,6 +30,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS (3-field node updates/s) & HBM roofline fraction; served solves/s, p99"
+L2_BYTES = 129e6  # GB300 L2
 BYTES_PER_NODE = {"fp64": 304, "fp32": 152, "bf16": 76, "fp16": 76}
 DTYPE = {"fp64": "f64", "fp32": "f32", "bf16": "f32 (bf16 storage)", "fp16": "f32 (fp16 storage)"}
 PROFILE_JSON = os.path.join(ROOT, "profiles", "roofline_counters.json")
@@ -232,7 +233,8 @@ def run_serving(args):
 
 def run_batch(args):
     """--workload batch: 256 uneven annulus-convection lattices (nr, nz ~
-    U{32..512}, seeds 0..255) advanced together by the batched step, replayed
+    U{32..512}, seeds 0..255; --instances, --batch-lo, --batch-hi change the
+    count and the size range) advanced together by the batched step, replayed
     from CUDA graphs; aggregate MLUPS and HBM roofline, and the Nu of the
     smallest instances against the oracle after the same steps."""
     import numpy as np
@@ -246,7 +248,7 @@ def run_batch(args):
     from paper_1806_10241_gb300.solver import Solver
     torch.cuda.set_device(0)
     storage = args.batch_storage
-    cases = W.batched_instances(args.instances)
+    cases = W.batched_instances(args.instances, lo=args.batch_lo, hi=args.batch_hi)
     stream = torch.cuda.Stream()
     solvers = []
     for cs in cases:
@@ -291,12 +293,14 @@ def run_batch(args):
     line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[storage], "data": "synthetic",
-            "config": {"workload": f"{len(cases)} annulus-convection lattices, nr, nz ~ U{{32..512}}, "
+            "config": {"workload": f"{len(cases)} annulus-convection lattices, nr, nz ~ U{{{args.batch_lo}..{args.batch_hi}}}, "
                                    "R_o/R_i ~ U[1.5,3], Ra log-U[1e3,1e5], inner swirl ~ U[0,0.05], seeds 0..",
                        "nodes": nodes, "storage": storage,
                        "launch": {"seg_rows": launch[0], "warps_per_block": launch[1], "row_fetch": launch[2],
                                   "graph_steps": args.graph_steps},
-                       "l2": "inputs larger than L2 (working set %.0f MB)" % (bpn * nodes / 1e6)},
+                       "l2": ("inputs larger than L2 (working set %.0f MB)" % (bpn * nodes / 1e6)
+                              if bpn * nodes > L2_BYTES else
+                              "working set %.0f MB fits in the L2: an L2-resident rate" % (bpn * nodes / 1e6))},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": float(peaks["hbm_gbs"]),
                          "unit": "GB/s", "frac": round(achieved / float(peaks["hbm_gbs"]), 4), "traffic": None,
                          "peak_kind": peak_kind, "algorithmic_bytes_per_node": bpn,
@@ -428,6 +432,8 @@ def main():
     ap.add_argument("--workload", default="cylinder", choices=["cylinder", "serving", "precision", "batch"])
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--batch-storage", dest="batch_storage", default="fp16", choices=["fp16", "bf16", "fp32"])
+    ap.add_argument("--batch-lo", dest="batch_lo", type=int, default=32)
+    ap.add_argument("--batch-hi", dest="batch_hi", type=int, default=512)
     ap.add_argument("--graph-steps", dest="graph_steps", type=int, default=10)
     ap.add_argument("--oracle-instances", dest="oracle_instances", type=int, default=3)
     ap.add_argument("--prec-steps", dest="prec_steps", type=int, default=2000)
