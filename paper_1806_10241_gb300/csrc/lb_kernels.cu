@@ -658,10 +658,18 @@ __device__ __forceinline__ void march(const KP<C> &k, const S *__restrict__ src,
 // allows the next launch to begin, then waits until every earlier grid of
 // the stream has completed and its writes are visible, before it reads or
 // writes any distribution.  Without the launch attribute both are no-ops.
-__device__ __forceinline__ void grid_dependency_trigger_and_wait()
+__device__ __forceinline__ void grid_dependency_trigger()
 {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dependency_wait()
+{
     asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dependency_trigger_and_wait()
+{
+    grid_dependency_trigger();
+    grid_dependency_wait();
 }
 
 template <typename S, typename C>
@@ -1251,8 +1259,12 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restric
     const int wpb = blockDim.x >> 5;
     unsigned char *ring = smem + batch3_ring_bytes<S>() * wib;
     KP<float> *skp = reinterpret_cast<KP<float> *>(smem + batch3_ring_bytes<S>() * wpb);
-    grid_dependency_trigger_and_wait();  // the previous step (or counter update) is complete
-    const unsigned long long t = t0 + (from_counter ? *(volatile const unsigned long long *)&ctl->counter : 0ULL);
+    // Programmatic dependent launch: the next step's blocks may become
+    // resident now.  The instance lookup and the parameter copy read only
+    // what no launch of the batch writes (the prefix sums, the descriptors),
+    // so they overlap the previous launch's last blocks; the step counter and
+    // the rows are read after the wait below.
+    grid_dependency_trigger();
     const int item = blockIdx.x * wpb + wib;
     if (item < total) {
         const int lo = batch_instance(prefix, n, item, lane);
@@ -1267,14 +1279,18 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restric
         const int local = item - prefix[lo];
         const int nw2 = bd->nwin2;
         const int w = local % nw2, sg = local / nw2;
-        const int cur = (bd->parity0 + (int)(t & 1ULL)) & 1;
         const int seg = bd->seg_rows;
         const int s = sg * seg, e = min(k.nz, s + seg);
         const bool has_m = s > 0 || k.xper, has_last = e < k.nz || k.xper;
-        const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(bd->map[cur]);
-        if (lane == 0)
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((unsigned long long)map)
+        if (lane < 2)
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                             (unsigned long long)bd->map[lane])
                          : "memory");
+        grid_dependency_wait();  // the previous launch is complete and its writes are visible
+        const unsigned long long t =
+            t0 + (from_counter ? *(volatile const unsigned long long *)&ctl->counter : 0ULL);
+        const int cur = (bd->parity0 + (int)(t & 1ULL)) & 1;
+        const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(bd->map[cur]);
         RowRing<S, R> rs;
         rs.map = map;
         rs.ring = ring;
