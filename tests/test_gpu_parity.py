@@ -346,6 +346,31 @@ def test_16bit_distributions_after_one_step_within_one_rounding(name, storage, m
     assert abs(np.mean((got - want) / tol)) < 0.05
 
 
+@pytest.mark.parametrize("storage,mant,scale", [("fp16", 10, 1024.0), ("bf16", 7, 1.0)])
+def test_16bit_full_size_one_step_within_one_rounding(storage, mant, scale):
+    """The benchmark lattice (1024 x 2048) in 16-bit storage with the launch
+    the benchmark times (6-row segments, rows read in place): one step from a
+    seeded state, every one of the 40 M stored values within one stochastic
+    rounding of the oracle's, the roundings unbiased over the lattice."""
+    c = W.config_cylinder(1024, 2048)
+    params = c.params
+    g = Solver(params, storage=storage)
+    assert g.get_launch() == (6, 1, 3)
+    g.set_dist(random_state(params, seed=23))
+    start = g.get_dist()
+    g.step(1)
+    got = g.get_dist()
+    o = oracle.Oracle(params)
+    o.set_dist(start)
+    o.step(1)
+    want = o.get_dist()
+    rest = np.concatenate([W9 * params["rho0"], np.zeros(5), W5 * params["T0"]])[:, None, None]
+    mag = np.maximum(np.abs(want - rest), np.abs(got - rest))
+    tol = _ulp16(mag * scale, mant) / scale + 2e-6
+    assert np.all(np.abs(got - want) <= tol), float(np.max(np.abs(got - want) / tol))
+    assert abs(np.mean((got - want) / tol)) < 0.01
+
+
 @pytest.mark.parametrize("switch", ["sign_literal", "explicit_sources"])
 @pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
 def test_reading_switches_match_oracle(switch, storage, tol):
