@@ -224,18 +224,22 @@ LB_EXPORT lb_status lb_get_launch(const lb_ctx *ctx, int32_t *seg_rows, int32_t 
  * of lb_required_bytes, which includes reduction scratch) or lend scratch.
  * dev_state points at one distribution buffer in the library's layout (the
  * bytes of an lb_get_state blob after its 16-byte header, 256-byte aligned);
- * desc and params describe it; step is copied to out->step.  The result
- * equals lb_diagnostics on the same state.
+ * desc and params describe it and pass the checks of lb_create and
+ * lb_set_params; step is copied to out->step.  The reductions use the
+ * default launch of the lattice: the result is bitwise that of
+ * lb_diagnostics on the same state under the default launch, and equal to
+ * reduction round-off under another launch (lb_set_launch, autotuning).
  *
  * Scratch: a 1 MiB array (2^17 doubles) in the library's static device
  * memory, which every GPU that loads the library holds until the process
  * exits.  A lattice needs 16 + 12 x (blocks <= 2048) + 4 (nr + nz) doubles;
  * larger lattices (nr + nz above about 26600) are rejected with LB_ERR_ARG.
- * No call allocates or frees memory.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and caches it: make that first
- * call before any stream capture.  Every call reuses the same array and clears
- * the part it uses; calls that overlap on the GPU (other streams, other
- * threads) race on it.  Synchronous on cuda_stream. */
+ * No call allocates or frees memory.  Every call looks up the array's device
+ * address in the current context (cudaGetSymbolAddress); the first call on a
+ * device may load the library's device code there, so make it before any
+ * stream capture.  Every call reuses the same array and clears the part it
+ * uses; calls that overlap on the GPU (other streams, other threads) race on
+ * it.  Synchronous on cuda_stream. */
 LB_EXPORT lb_status lb_diagnostics_static(const lb_grid_desc *desc, const lb_params *params,
                                           const void *dev_state, int64_t step, void *cuda_stream,
                                           lb_diag *out);

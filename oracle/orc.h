@@ -7,9 +7,10 @@
  * use it.  It shares no code, header, table or constant with the CUDA library.
  *
  * It is a literal, slow, unfused transcription of the paper's algorithm:
+ *   pass 0: macroscopic fields of the stored (post-collision) state;
  *   pass 1: pull streaming with boundary rules, output moments (Eq. 16b, 18,
  *           33b, 35, 46b, 47);
- *   pass 2: central-difference gradients of the same-step output fields,
+ *   pass 2: central-difference gradients of the pass-0 fields,
  *           geometric sources (Eq. 4, 5, 7, 9), pre-collision half step
  *           (Eq. 21, 38, 48), cascaded collisions (Eq. 17, 34, 49), source
  *           moments (Eq. 26, 41, 51), back-transforms (Eq. 27, 42, 52).

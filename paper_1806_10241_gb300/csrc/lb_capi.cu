@@ -51,12 +51,6 @@ namespace {
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-int pitch_for(int nr, int storage)
-{
-    const int m = lbk::storage_bytes(storage) == 2 ? 64 : 32;
-    return (nr + m - 1) / m * m;
-}
-
 lb_status fail(lb_ctx *ctx, lb_status st, const char *fmt, ...)
 {
     char *dst = ctx ? ctx->err : g_err;
@@ -72,17 +66,23 @@ lb_status cuda_fail(lb_ctx *ctx, cudaError_t e, const char *what)
     return fail(ctx, LB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+lb_status say(char *err, size_t n, lb_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(err, n, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
 lb_status check_desc(const lb_grid_desc *d, size_t *plane, size_t *dist_bytes)
 {
-    if (!d) return fail(nullptr, LB_ERR_ARG, "desc is NULL");
-    if (d->nr < 2 || d->nz < 2) return fail(nullptr, LB_ERR_ARG, "nr and nz must be >= 2 (got %d, %d)", d->nr, d->nz);
-    if (d->nr > (1 << 20) || d->nz > (1 << 24)) return fail(nullptr, LB_ERR_ARG, "lattice too large");
-    if (!(d->r_inner >= 0.0) || !std::isfinite(d->r_inner)) return fail(nullptr, LB_ERR_ARG, "r_inner must be >= 0");
-    if (d->storage < LB_FP64 || d->storage > LB_FP16) return fail(nullptr, LB_ERR_ARG, "unknown storage %d", d->storage);
-    if (d->reserved != 0) return fail(nullptr, LB_ERR_ARG, "reserved must be 0");
-    const size_t p = (size_t)d->nz * (size_t)pitch_for(d->nr, d->storage);
-    *plane = p;
-    *dist_bytes = align256(lbk::NQ * p * lbk::storage_bytes(d->storage));
+    HostParams h;
+    std::memset(&h, 0, sizeof(h));
+    const lb_status st = lbk::host_from_desc(d, &h, g_err, sizeof(g_err));
+    if (st != LB_OK) return st;
+    *plane = (size_t)h.plane;
+    *dist_bytes = align256(lbk::NQ * (size_t)h.plane * lbk::storage_bytes(d->storage));
     return LB_OK;
 }
 
@@ -90,35 +90,88 @@ size_t scratch_bytes() { return align256((size_t)lbk::MAX_DIAG_BLOCKS * lbk::NSU
 
 size_t table_bytes(int pitch) { return align256(2 * (size_t)pitch * sizeof(float)); }
 
-lb_status validate_params(lb_ctx *ctx, const lb_params *p)
+}  // namespace
+
+int lbk::pitch_for(int nr, int storage)
 {
-    const HostParams &h = ctx->hp;
+    const int m = lbk::storage_bytes(storage) == 2 ? 64 : 32;
+    return (nr + m - 1) / m * m;
+}
+
+lb_status lbk::host_from_desc(const lb_grid_desc *d, HostParams *h, char *err, size_t n)
+{
+    if (!d) return say(err, n, LB_ERR_ARG, "desc is NULL");
+    if (d->nr < 2 || d->nz < 2) return say(err, n, LB_ERR_ARG, "nr and nz must be >= 2 (got %d, %d)", d->nr, d->nz);
+    if (d->nr > (1 << 20) || d->nz > (1 << 24)) return say(err, n, LB_ERR_ARG, "lattice too large");
+    if (!(d->r_inner >= 0.0) || !std::isfinite(d->r_inner)) return say(err, n, LB_ERR_ARG, "r_inner must be >= 0");
+    if (d->storage < LB_FP64 || d->storage > LB_FP16)
+        return say(err, n, LB_ERR_ARG, "unknown storage %d", d->storage);
+    if (d->reserved != 0) return say(err, n, LB_ERR_ARG, "reserved must be 0");
+    h->nr = d->nr;
+    h->nz = d->nz;
+    h->pitch = pitch_for(d->nr, d->storage);
+    h->plane = (long long)h->nz * h->pitch;
+    h->storage = d->storage;
+    h->r0 = d->r_inner;
+    h->scale = d->storage == LB_FP16 ? lbk::kFp16Scale : 1.0;
+    return LB_OK;
+}
+
+lb_status lbk::host_set_params(const lb_params *p, HostParams *h, char *err, size_t n)
+{
+    if (!p) return say(err, n, LB_ERR_ARG, "params is NULL");
     if (!(p->nu > 0.0) || !(p->alpha > 0.0) || !(p->rho0 > 0.0))
-        return fail(ctx, LB_ERR_ARG, "nu, alpha and rho0 must be > 0");
+        return say(err, n, LB_ERR_ARG, "nu, alpha and rho0 must be > 0");
     if (!(p->omega3 > 0.0 && p->omega3 < 2.0) || !(p->omega_hi > 0.0 && p->omega_hi < 2.0))
-        return fail(ctx, LB_ERR_ARG, "omega3 and omega_hi must lie in (0, 2)");
+        return say(err, n, LB_ERR_ARG, "omega3 and omega_hi must lie in (0, 2)");
+    const double vals[] = {p->g_beta, p->T0, p->body_fx};
+    for (double v : vals)
+        if (!std::isfinite(v)) return say(err, n, LB_ERR_ARG, "non-finite g_beta, T0 or body_fx");
     const int per0 = p->side[0].flow == LB_FLOW_PERIODIC, per1 = p->side[1].flow == LB_FLOW_PERIODIC;
-    if (per0 != per1) return fail(ctx, LB_ERR_ARG, "periodicity needs both end sides");
+    if (per0 != per1) return say(err, n, LB_ERR_ARG, "periodicity needs both end sides");
     for (int s = 0; s < 4; ++s) {
         const lb_side &sd = p->side[s];
         if (sd.flow < 0 || sd.flow > 2 || sd.swirl < 0 || sd.swirl > 3 || sd.heat < 0 || sd.heat > 3)
-            return fail(ctx, LB_ERR_ARG, "side %d: unknown boundary code", s);
+            return say(err, n, LB_ERR_ARG, "side %d: unknown boundary code", s);
         const bool per = sd.flow == LB_FLOW_PERIODIC;
         const bool ax = sd.flow == LB_FLOW_AXIS;
         if ((sd.swirl == LB_SC_PERIODIC) != per || (sd.heat == LB_SC_PERIODIC) != per)
-            return fail(ctx, LB_ERR_ARG, "side %d: periodic must apply to f, g and h together", s);
+            return say(err, n, LB_ERR_ARG, "side %d: periodic must apply to f, g and h together", s);
         if ((sd.swirl == LB_SC_AXIS) != ax || (sd.heat == LB_SC_AXIS) != ax)
-            return fail(ctx, LB_ERR_ARG, "side %d: the axis must apply to f, g and h together", s);
-        if (per && s >= 2) return fail(ctx, LB_ERR_ARG, "periodicity only along z");
-        if (ax && (s != 2 || h.r0 != 0.0)) return fail(ctx, LB_ERR_ARG, "the axis is only the inner side of a cylinder");
-        const double vals[4] = {sd.u_wx, sd.u_wy, sd.omega, sd.T_w};
-        for (double v : vals)
-            if (!std::isfinite(v)) return fail(ctx, LB_ERR_ARG, "side %d: non-finite wall value", s);
+            return say(err, n, LB_ERR_ARG, "side %d: the axis must apply to f, g and h together", s);
+        if (per && s >= 2) return say(err, n, LB_ERR_ARG, "periodicity only along z");
+        if (ax && (s != 2 || h->r0 != 0.0))
+            return say(err, n, LB_ERR_ARG, "the axis is only the inner side of a cylinder");
+        const double wv[4] = {sd.u_wx, sd.u_wy, sd.omega, sd.T_w};
+        for (double v : wv)
+            if (!std::isfinite(v)) return say(err, n, LB_ERR_ARG, "side %d: non-finite wall value", s);
     }
-    if (h.r0 == 0.0 && !p->planar && p->side[2].flow != LB_FLOW_AXIS)
-        return fail(ctx, LB_ERR_ARG, "r_inner = 0 needs the axis on the inner side");
+    if (h->r0 == 0.0 && !p->planar && p->side[2].flow != LB_FLOW_AXIS)
+        return say(err, n, LB_ERR_ARG, "r_inner = 0 needs the axis on the inner side");
+    h->nu = p->nu;
+    h->alpha = p->alpha;
+    h->omega3 = p->omega3;
+    h->omega_hi = p->omega_hi;
+    h->g_beta = p->g_beta;
+    h->T0 = p->T0;
+    h->body_fx = p->body_fx;
+    h->rho0 = p->rho0;
+    h->planar = p->planar;
+    h->sign_literal = p->sign_literal;
+    h->explicit_sources = p->explicit_sources;
+    for (int s = 0; s < 4; ++s) {
+        h->flow[s] = p->side[s].flow;
+        h->swirl[s] = p->side[s].swirl;
+        h->heat[s] = p->side[s].heat;
+        h->uwx[s] = p->side[s].u_wx;
+        h->uwy[s] = p->side[s].u_wy;
+        h->omega[s] = p->side[s].omega;
+        h->Tw[s] = p->side[s].T_w;
+    }
     return LB_OK;
 }
+
+namespace {
 
 // Rows of `planes` doubles per node that fit in the staging area.
 lb_status staging(lb_ctx *ctx, int planes, double **ptr, int *rows)
@@ -170,7 +223,7 @@ lb_status lb_required_bytes(const lb_grid_desc *desc, size_t *bytes)
     lb_status st = check_desc(desc, &plane, &dist);
     if (st != LB_OK) return st;
     if (!bytes) return fail(nullptr, LB_ERR_ARG, "bytes is NULL");
-    *bytes = 2 * dist + scratch_bytes() + table_bytes(pitch_for(desc->nr, desc->storage));
+    *bytes = 2 * dist + scratch_bytes() + table_bytes(lbk::pitch_for(desc->nr, desc->storage));
     return LB_OK;
 }
 
@@ -181,7 +234,7 @@ lb_status lb_create(const lb_grid_desc *desc, void *dev_buf, size_t bytes, void 
     size_t plane, dist;
     lb_status st = check_desc(desc, &plane, &dist);
     if (st != LB_OK) return st;
-    const size_t need = 2 * dist + scratch_bytes() + table_bytes(pitch_for(desc->nr, desc->storage));
+    const size_t need = 2 * dist + scratch_bytes() + table_bytes(lbk::pitch_for(desc->nr, desc->storage));
     if (!dev_buf) return fail(nullptr, LB_ERR_ARG, "dev_buf is NULL");
     if (((uintptr_t)dev_buf & 255) != 0) return fail(nullptr, LB_ERR_ARG, "dev_buf must be 256-byte aligned");
     if (bytes < need) return fail(nullptr, LB_ERR_NOMEM, "buffer holds %zu bytes, %zu needed", bytes, need);
@@ -189,13 +242,7 @@ lb_status lb_create(const lb_grid_desc *desc, void *dev_buf, size_t bytes, void 
     if (!c) return fail(nullptr, LB_ERR_NOMEM, "host allocation failed");
     HostParams &h = c->hp;
     std::memset(&h, 0, sizeof(h));
-    h.nr = desc->nr;
-    h.nz = desc->nz;
-    h.pitch = pitch_for(desc->nr, desc->storage);
-    h.plane = (long long)plane;
-    h.storage = desc->storage;
-    h.r0 = desc->r_inner;
-    h.scale = desc->storage == LB_FP16 ? lbk::kFp16Scale : 1.0;
+    lbk::host_from_desc(desc, &h, g_err, sizeof(g_err));  // checked above
     c->buf = (char *)dev_buf;
     c->bytes = bytes;
     c->dist_bytes = dist;
@@ -220,29 +267,9 @@ lb_status lb_create(const lb_grid_desc *desc, void *dev_buf, size_t bytes, void 
 lb_status lb_set_params(lb_ctx *ctx, const lb_params *p)
 {
     if (!ctx || !p) return fail(ctx, LB_ERR_ARG, "NULL argument");
-    lb_status st = validate_params(ctx, p);
+    lb_status st = lbk::host_set_params(p, &ctx->hp, ctx->err, sizeof(ctx->err));
     if (st != LB_OK) return st;
     HostParams &h = ctx->hp;
-    h.nu = p->nu;
-    h.alpha = p->alpha;
-    h.omega3 = p->omega3;
-    h.omega_hi = p->omega_hi;
-    h.g_beta = p->g_beta;
-    h.T0 = p->T0;
-    h.body_fx = p->body_fx;
-    h.rho0 = p->rho0;
-    h.planar = p->planar;
-    h.sign_literal = p->sign_literal;
-    h.explicit_sources = p->explicit_sources;
-    for (int s = 0; s < 4; ++s) {
-        h.flow[s] = p->side[s].flow;
-        h.swirl[s] = p->side[s].swirl;
-        h.heat[s] = p->side[s].heat;
-        h.uwx[s] = p->side[s].u_wx;
-        h.uwy[s] = p->side[s].u_wy;
-        h.omega[s] = p->side[s].omega;
-        h.Tw[s] = p->side[s].T_w;
-    }
     // rest state: every stored deviation is zero; clear the status word;
     // radius table (entries past nr - 1 repeat the last radius)
     std::vector<float> tab(2 * (size_t)h.pitch);

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "../../include/lb.h"
+
 namespace lbk {
 
 enum Mode { MODE_STEP = 0, MODE_FIELDS = 1, MODE_DIAG = 2, MODE_DIAG_STRIP = 3 };
@@ -38,6 +40,19 @@ struct Launch {
     int warps_per_block;
     int use_tma;              // FP32 / 16-bit rows: 0 plain loads, 1 TMA ring, 2 TMA ring read in place
 };
+
+// Elements per row of a plane: nr rounded up to 32 (4- and 8-byte storage)
+// or 64 (2-byte storage) elements.
+int pitch_for(int nr, int storage);
+// The lattice part of h (shape, pitch, storage, storage scale) from a grid
+// descriptor, after the checks lb_required_bytes and lb_create make.  On
+// failure h is untouched and err (n bytes) holds a one-line message.
+lb_status host_from_desc(const lb_grid_desc *d, HostParams *h, char *err, size_t n);
+// The physical part of h from lb_params, after the checks lb_set_params
+// makes (relaxation rates, boundary codes and their pairing, the axis only on
+// the inner side of a cylinder, finite wall values); needs the lattice part
+// (r0).  On failure h is untouched and err holds a one-line message.
+lb_status host_set_params(const lb_params *p, HostParams *h, char *err, size_t n);
 
 // One time step src -> dst; `step` seeds the stochastic rounding of 16-bit
 // storage.

@@ -23,7 +23,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <type_traits>
 
 #include <cuda.h>
@@ -1794,8 +1793,11 @@ cudaError_t launch_batch_diag(int storage, const void *desc, const void *bdiag, 
 // array below (1 MiB, allocated by the CUDA runtime when the module loads on
 // a device and held by every device that loads the library until the process
 // exits).  Host code must not pass the array's name to a kernel -- in host
-// code it is only a stand-in for the symbol -- so the device address is looked
-// up once per device with cudaGetSymbolAddress and cached.
+// code it is only a stand-in for the symbol -- so every call looks up the
+// device address of the array in the current device's context with
+// cudaGetSymbolAddress.  The address is not cached: after cudaDeviceReset, or
+// under another context on the same device, the module is loaded again at
+// another address.
 
 static __device__ __align__(256) double g_diag_scratch[1 << 17];
 
@@ -1804,25 +1806,13 @@ namespace {
 
 constexpr size_t kScratchDoubles = (size_t)1 << 17;
 constexpr int kScratchMaxBlocks = 2048;
-constexpr int kMaxDevices = 256;
-
-std::mutex g_scratch_mu;
-double *g_scratch_ptr[kMaxDevices] = {};
 
 cudaError_t scratch_address(double **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_diag_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_diag_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = (double *)p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = (double *)p;
     return cudaSuccess;
 }
 
@@ -1851,48 +1841,18 @@ extern "C" lb_status lb_diagnostics_static(const lb_grid_desc *desc, const lb_pa
         set_global_error("lb_diagnostics_static: NULL argument");
         return LB_ERR_ARG;
     }
-    if (desc->nr < 2 || desc->nz < 2 || desc->storage < LB_FP64 || desc->storage > LB_FP16 || desc->reserved != 0 ||
-        !(desc->r_inner >= 0.0) || !std::isfinite(desc->r_inner)) {
-        set_global_error("lb_diagnostics_static: invalid grid descriptor");
-        return LB_ERR_ARG;
-    }
-    if (!(p->nu > 0.0) || !(p->alpha > 0.0) || !(p->rho0 > 0.0)) {
-        set_global_error("lb_diagnostics_static: nu, alpha and rho0 must be > 0");
+    HostParams h;
+    std::memset(&h, 0, sizeof(h));
+    char why[200];
+    if (host_from_desc(desc, &h, why, sizeof(why)) != LB_OK || host_set_params(p, &h, why, sizeof(why)) != LB_OK) {
+        char msg[256];
+        snprintf(msg, sizeof(msg), "lb_diagnostics_static: %s", why);
+        set_global_error(msg);
         return LB_ERR_ARG;
     }
     if (((uintptr_t)dev_state & 255) != 0) {
         set_global_error("lb_diagnostics_static: dev_state must be 256-byte aligned");
         return LB_ERR_ARG;
-    }
-    HostParams h;
-    std::memset(&h, 0, sizeof(h));
-    const int m = storage_bytes(desc->storage) == 2 ? 64 : 32;
-    h.nr = desc->nr;
-    h.nz = desc->nz;
-    h.pitch = (desc->nr + m - 1) / m * m;
-    h.plane = (long long)h.nz * h.pitch;
-    h.storage = desc->storage;
-    h.r0 = desc->r_inner;
-    h.scale = desc->storage == LB_FP16 ? 1024.0 : 1.0;
-    h.nu = p->nu;
-    h.alpha = p->alpha;
-    h.omega3 = p->omega3;
-    h.omega_hi = p->omega_hi;
-    h.g_beta = p->g_beta;
-    h.T0 = p->T0;
-    h.body_fx = p->body_fx;
-    h.rho0 = p->rho0;
-    h.planar = p->planar;
-    h.sign_literal = p->sign_literal;
-    h.explicit_sources = p->explicit_sources;
-    for (int s = 0; s < 4; ++s) {
-        h.flow[s] = p->side[s].flow;
-        h.swirl[s] = p->side[s].swirl;
-        h.heat[s] = p->side[s].heat;
-        h.uwx[s] = p->side[s].u_wx;
-        h.uwy[s] = p->side[s].u_wy;
-        h.omega[s] = p->side[s].omega;
-        h.Tw[s] = p->side[s].T_w;
     }
     // launch shape within the static scratch: at most kScratchMaxBlocks blocks
     Launch l = default_launch(h);
