@@ -128,8 +128,14 @@ typedef struct {
  * (lateral wall of radius R_w: -R_w / (H dT) sum dT/dr; end wall:
  * -(H / dT) (2 / (R_o^2 - R_i^2)) sum dT/dz r), the mean of the two
  * opposite heated sides, total mass (sum of f), radius-weighted mass, sum
- * of T and max |u| in the meridian plane -- all accumulated in FP64 from the
- * pre-collision fields of the current state. */
+ * of T and max |u| in the meridian plane, and the mean equivalent
+ * conductivity of the inner and outer wall of an annulus (Sec. 3.5):
+ * k_eq = ln(R_o / R_i) / (H dT) sum over z of (-R_w dT/dr) at the wall,
+ * 1 for pure conduction (0 on a side that is not a Dirichlet-T lateral wall
+ * of an annulus) -- all accumulated in FP64 from the pre-collision fields of
+ * the current state.  Wall derivatives are one-sided and second order
+ * through the wall value, (-8 T_w + 9 T_1 - T_2) / 3 along the inward
+ * normal; sums over the wall are midpoint sums. */
 typedef struct {
     double nu_side[4];
     double nu_i, nu_o, nu_avg;
@@ -137,6 +143,7 @@ typedef struct {
     int64_t step;
     int32_t status;  /* LB_OK or LB_ERR_DIVERGED                          */
     int32_t pad;
+    double k_eq_i, k_eq_o;
 } lb_diag;
 
 /* Bytes of device memory a lattice of this shape needs (2 distribution

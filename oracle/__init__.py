@@ -47,7 +47,8 @@ class Params(C.Structure):
 class Diag(C.Structure):
     _fields_ = [("nu_side", C.c_double * 4), ("nu_i", C.c_double), ("nu_o", C.c_double),
                 ("nu_avg", C.c_double), ("mass", C.c_double), ("mass_r", C.c_double),
-                ("T_sum", C.c_double), ("u_max", C.c_double), ("step", C.c_int64)]
+                ("T_sum", C.c_double), ("u_max", C.c_double), ("step", C.c_int64),
+                ("k_eq_i", C.c_double), ("k_eq_o", C.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -191,7 +192,8 @@ class Oracle:
         lib().orc_diag_compute(self._h, C.byref(d))
         return {"nu_side": list(d.nu_side), "nu_i": d.nu_i, "nu_o": d.nu_o,
                 "nu_avg": d.nu_avg, "mass": d.mass, "mass_r": d.mass_r,
-                "T_sum": d.T_sum, "u_max": d.u_max, "step": int(d.step)}
+                "T_sum": d.T_sum, "u_max": d.u_max, "k_eq_i": d.k_eq_i, "k_eq_o": d.k_eq_o,
+                "step": int(d.step)}
 
     def stream_function(self) -> tuple:
         """(psi [nz, nr] on the cell faces y = r0 + j + 1, max |psi|)."""

@@ -683,6 +683,25 @@ int orc_diag_compute(const orc_state *s, orc_diag *out)
         for (int i = 0; i < nz; ++i) sum += (8.0 * Tw - 9.0 * TT(i, nr - 1) + TT(i, nr - 2)) / 3.0;
         out->nu_side[3] = -Ro / (H * dT) * sum;
     }
+    /* mean equivalent conductivity of a lateral wall of an annulus (Sec. 3.5):
+     * k_eq = ln(R_o / R_i) / (H dT) * integral over z of (-r dT/dr) at the
+     * wall, the integral a midpoint sum over the rows, dT/dr the same
+     * one-sided wall derivative as above */
+    if (Ri > 0.0) {
+        const double lg = log(Ro / Ri);
+        if (p->side[2].heat == ORC_SC_DIRICHLET) {
+            const double Tw = p->side[2].T_w;
+            double integral = 0;
+            for (int i = 0; i < nz; ++i) integral += -Ri * (-8.0 * Tw + 9.0 * TT(i, 0) - TT(i, 1)) / 3.0;
+            out->k_eq_i = lg / (H * dT) * integral;
+        }
+        if (p->side[3].heat == ORC_SC_DIRICHLET) {
+            const double Tw = p->side[3].T_w;
+            double integral = 0;
+            for (int i = 0; i < nz; ++i) integral += -Ro * (8.0 * Tw - 9.0 * TT(i, nr - 1) + TT(i, nr - 2)) / 3.0;
+            out->k_eq_o = lg / (H * dT) * integral;
+        }
+    }
     const double area = 0.5 * (Ro * Ro - Ri * Ri);
     if (p->side[0].heat == ORC_SC_DIRICHLET) {
         const double Tw = p->side[0].T_w;

@@ -83,6 +83,8 @@ typedef struct {
     double nu_i, nu_o, nu_avg;
     double mass, mass_r, T_sum, u_max;
     int64_t step;
+    double k_eq_i, k_eq_o; /* equivalent conductivity of the lateral walls of
+                              an annulus (Sec. 3.5), else 0                 */
 } orc_diag;
 
 typedef struct orc_state orc_state;

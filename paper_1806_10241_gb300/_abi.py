@@ -43,7 +43,8 @@ class lb_diag(C.Structure):
     _fields_ = [("nu_side", C.c_double * 4), ("nu_i", C.c_double), ("nu_o", C.c_double),
                 ("nu_avg", C.c_double), ("mass", C.c_double), ("mass_r", C.c_double),
                 ("T_sum", C.c_double), ("u_max", C.c_double), ("step", C.c_int64),
-                ("status", C.c_int32), ("pad", C.c_int32)]
+                ("status", C.c_int32), ("pad", C.c_int32), ("k_eq_i", C.c_double),
+                ("k_eq_o", C.c_double)]
 
 
 _vp = C.c_void_p

@@ -171,6 +171,40 @@ lb_status lbk::host_set_params(const lb_params *p, HostParams *h, char *err, siz
     return LB_OK;
 }
 
+void lbk::diag_from_sums(const HostParams &h, const double *res, int kstatus, int64_t step, lb_diag *out)
+{
+    std::memset(out, 0, sizeof(*out));
+    const double N = (double)h.nr * h.nz;
+    const double sum_y = (double)h.nz * (h.nr * h.r0 + 0.5 * (double)h.nr * h.nr);
+    out->mass = h.rho0 * N + res[0];
+    out->mass_r = h.rho0 * sum_y + res[1];
+    out->T_sum = res[2];
+    out->u_max = res[3];
+    for (int s = 0; s < 4; ++s) out->nu_side[s] = res[4 + s];
+    int a = -1, b = -1;
+    if (h.heat[2] == LB_SC_DIRICHLET && h.heat[3] == LB_SC_DIRICHLET) {
+        a = 2;
+        b = 3;
+    } else if (h.heat[0] == LB_SC_DIRICHLET && h.heat[1] == LB_SC_DIRICHLET) {
+        a = 0;
+        b = 1;
+    } else {
+        for (int s = 0; s < 4; ++s)
+            if (h.heat[s] == LB_SC_DIRICHLET) {
+                if (a < 0) a = s;
+                else if (b < 0) b = s;
+            }
+    }
+    if (a >= 0) out->nu_i = out->nu_side[a];
+    if (b >= 0) out->nu_o = out->nu_side[b];
+    out->nu_avg = (a >= 0 && b >= 0) ? 0.5 * (out->nu_i + out->nu_o) : out->nu_i;
+    out->k_eq_i = res[9];
+    out->k_eq_o = res[10];
+    out->step = step;
+    const bool bad = res[8] > 0.0 || !std::isfinite(res[0]) || !std::isfinite(res[2]);
+    out->status = kstatus ? kstatus : (bad ? LB_ERR_DIVERGED : LB_OK);
+}
+
 namespace {
 
 // Rows of `planes` doubles per node that fit in the staging area.
@@ -413,35 +447,7 @@ lb_status lb_stream_function(lb_ctx *ctx, double *host_psi, double *psi_max)
 // lb_diag from the NSUM device sums of the diagnostics and the status word
 static void fill_diag(const lb_ctx *ctx, const double *res, int kstatus, lb_diag *out)
 {
-    const HostParams &h = ctx->hp;
-    std::memset(out, 0, sizeof(*out));
-    const double N = (double)h.nr * h.nz;
-    const double sum_y = (double)h.nz * (h.nr * h.r0 + 0.5 * (double)h.nr * h.nr);
-    out->mass = h.rho0 * N + res[0];
-    out->mass_r = h.rho0 * sum_y + res[1];
-    out->T_sum = res[2];
-    out->u_max = res[3];
-    for (int s = 0; s < 4; ++s) out->nu_side[s] = res[4 + s];
-    int a = -1, b = -1;
-    if (h.heat[2] == LB_SC_DIRICHLET && h.heat[3] == LB_SC_DIRICHLET) {
-        a = 2;
-        b = 3;
-    } else if (h.heat[0] == LB_SC_DIRICHLET && h.heat[1] == LB_SC_DIRICHLET) {
-        a = 0;
-        b = 1;
-    } else {
-        for (int s = 0; s < 4; ++s)
-            if (h.heat[s] == LB_SC_DIRICHLET) {
-                if (a < 0) a = s;
-                else if (b < 0) b = s;
-            }
-    }
-    if (a >= 0) out->nu_i = out->nu_side[a];
-    if (b >= 0) out->nu_o = out->nu_side[b];
-    out->nu_avg = (a >= 0 && b >= 0) ? 0.5 * (out->nu_i + out->nu_o) : out->nu_i;
-    out->step = ctx->step;
-    const bool bad = res[8] > 0.0 || !std::isfinite(res[0]) || !std::isfinite(res[2]);
-    out->status = kstatus ? kstatus : (bad ? LB_ERR_DIVERGED : LB_OK);
+    lbk::diag_from_sums(ctx->hp, res, kstatus, ctx->step, out);
 }
 
 lb_status lb_diagnostics(lb_ctx *ctx, lb_diag *out)

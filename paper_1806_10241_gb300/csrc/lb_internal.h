@@ -54,6 +54,10 @@ lb_status host_from_desc(const lb_grid_desc *d, HostParams *h, char *err, size_t
 // (r0).  On failure h is untouched and err holds a one-line message.
 lb_status host_set_params(const lb_params *p, HostParams *h, char *err, size_t n);
 
+// lb_diag from the NSUM sums of the diagnostics (result[] of launch_diag),
+// the device status word (LB_OK, else reported as the status) and the step.
+void diag_from_sums(const HostParams &h, const double *res, int kstatus, int64_t step, lb_diag *out);
+
 // One time step src -> dst; `step` seeds the stochastic rounding of 16-bit
 // storage.
 cudaError_t launch_step(const HostParams &p, const Launch &l, const void *src, void *dst,
@@ -74,7 +78,8 @@ cudaError_t launch_psi(const double *ux, double *psi, double *rowmax, int nrows,
 // Diagnostics of the stored state src: block partial sums (partial), the
 // pre-collision T field (tfield, nz * nr doubles of scratch) and the final
 // values in result[NSUM]: 0 sum(rho - rho0), 1 sum((rho - rho0) y), 2 sum T,
-// 3 max |u|, 4..7 Nusselt number per side, 8 divergence flag.
+// 3 max |u|, 4..7 Nusselt number per side, 8 divergence flag, 9 / 10 the
+// equivalent conductivity k_eq of the inner / outer wall of an annulus.
 cudaError_t launch_diag(const HostParams &p, const Launch &l, const void *src, double *partial,
                         double *tfield, double *result, cudaStream_t s);
 // Equilibria of host-format fields [5][rows][nr] (double) into rows [row0,row1) of dst.

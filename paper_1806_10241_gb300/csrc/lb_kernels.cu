@@ -92,8 +92,8 @@ template <typename C> struct KP {
     C scale, inv_scale;
     C r0c, roc;           // inner and outer wall radii, rounded once
     const float *ytab;    // y[pitch] then 1/y[pitch] (pair kernels)
-    // Nusselt scales per side (diagnostics)
-    double nu_scale[4];
+    // Nusselt and equivalent-conductivity scales per side (diagnostics)
+    double nu_scale[4], keq_scale[4];
 };
 
 template <typename C> KP<C> make_kp(const HostParams &h)
@@ -149,6 +149,12 @@ template <typename C> KP<C> make_kp(const HostParams &h)
     k.nu_scale[0] = k.nu_scale[1] = -(H / dT) * 2.0 / (Ro * Ro - Ri * Ri);
     k.nu_scale[2] = -Ri / (H * dT);
     k.nu_scale[3] = -Ro / (H * dT);
+    // mean equivalent conductivity of a lateral wall of an annulus (Sec. 3.5):
+    // ln(R_o / R_i) / (H dT) times the sum over z of -R_w dT/dr
+    const double lg = Ri > 0.0 ? std::log(Ro / Ri) : 0.0;
+    k.keq_scale[0] = k.keq_scale[1] = 0.0;
+    k.keq_scale[2] = -Ri * lg / (H * dT);
+    k.keq_scale[3] = -Ro * lg / (H * dT);
     return k;
 }
 
@@ -937,7 +943,10 @@ __device__ __forceinline__ void wall_block(const KP<C> &k, const double *__restr
             if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
             __syncthreads();
         }
-        if (threadIdx.x == 0) result[4 + sd] = k.heat[sd] == 0 ? sh[0] * k.nu_scale[sd] : 0.0;
+        if (threadIdx.x == 0) {
+            result[4 + sd] = k.heat[sd] == 0 ? sh[0] * k.nu_scale[sd] : 0.0;
+            if (sd >= 2) result[7 + sd] = k.heat[sd] == 0 ? sh[0] * k.keq_scale[sd] : 0.0;  // 9, 10: k_eq
+        }
         __syncthreads();
     }
 }
@@ -1008,7 +1017,10 @@ __global__ void __launch_bounds__(256) k_wall_strip(KP<C> k, const double *__res
             if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
             __syncthreads();
         }
-        if (threadIdx.x == 0) result[4 + sd] = k.heat[sd] == 0 ? sh[0] * k.nu_scale[sd] : 0.0;
+        if (threadIdx.x == 0) {
+            result[4 + sd] = k.heat[sd] == 0 ? sh[0] * k.nu_scale[sd] : 0.0;
+            if (sd >= 2) result[7 + sd] = k.heat[sd] == 0 ? sh[0] * k.keq_scale[sd] : 0.0;  // 9, 10: k_eq
+        }
         __syncthreads();
     }
 }
@@ -1020,7 +1032,7 @@ __device__ __forceinline__ void diag_final_block(const double *__restrict__ part
 {
     __shared__ double sh[256];
     for (int q = 0; q < NSUM; ++q) {
-        if (q >= 4 && q < 8) continue;  // 4..7: wall sums (k_wall)
+        if ((q >= 4 && q < 8) || q == 9 || q == 10) continue;  // 4..7, 9, 10: wall sums (k_wall)
         const bool mx = q == 3 || q == 8;
         double r = 0.0;
         for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
@@ -1897,33 +1909,6 @@ extern "C" lb_status lb_diagnostics_static(const lb_grid_desc *desc, const lb_pa
         set_global_error(msg);
         return LB_ERR_CUDA;
     }
-    std::memset(out, 0, sizeof(*out));
-    const double N = (double)h.nr * h.nz;
-    const double sum_y = (double)h.nz * (h.nr * h.r0 + 0.5 * (double)h.nr * h.nr);
-    out->mass = h.rho0 * N + res[0];
-    out->mass_r = h.rho0 * sum_y + res[1];
-    out->T_sum = res[2];
-    out->u_max = res[3];
-    for (int s = 0; s < 4; ++s) out->nu_side[s] = res[4 + s];
-    int a = -1, b = -1;
-    if (h.heat[2] == LB_SC_DIRICHLET && h.heat[3] == LB_SC_DIRICHLET) {
-        a = 2;
-        b = 3;
-    } else if (h.heat[0] == LB_SC_DIRICHLET && h.heat[1] == LB_SC_DIRICHLET) {
-        a = 0;
-        b = 1;
-    } else {
-        for (int s = 0; s < 4; ++s)
-            if (h.heat[s] == LB_SC_DIRICHLET) {
-                if (a < 0) a = s;
-                else if (b < 0) b = s;
-            }
-    }
-    if (a >= 0) out->nu_i = out->nu_side[a];
-    if (b >= 0) out->nu_o = out->nu_side[b];
-    out->nu_avg = (a >= 0 && b >= 0) ? 0.5 * (out->nu_i + out->nu_o) : out->nu_i;
-    out->step = step;
-    const bool bad = res[8] > 0.0 || !std::isfinite(res[0]) || !std::isfinite(res[2]);
-    out->status = bad ? LB_ERR_DIVERGED : LB_OK;
+    diag_from_sums(h, res, 0, step, out);
     return LB_OK;
 }

@@ -30,7 +30,7 @@ def diag_dict(d) -> dict:
     """lb_diag as a dict."""
     return {"nu_side": list(d.nu_side), "nu_i": d.nu_i, "nu_o": d.nu_o, "nu_avg": d.nu_avg,
             "mass": d.mass, "mass_r": d.mass_r, "T_sum": d.T_sum, "u_max": d.u_max,
-            "step": int(d.step), "status": int(d.status)}
+            "k_eq_i": d.k_eq_i, "k_eq_o": d.k_eq_o, "step": int(d.step), "status": int(d.status)}
 
 
 class Solver:

@@ -227,15 +227,6 @@ def mixed_convection_annulus(D: int = 40, eta: float = 10.0, ratio: float = 2.0,
     return Case("mixed_convection_annulus", params, rest_fields(nz, nr, T))
 
 
-def k_eq_inner(params: dict, nu_inner: float) -> float:
-    """Mean equivalent conductivity at the inner cylinder (Sec. 3.5):
-    ln(R_o / R_i) / (H dT) * integral over z of (-r dT/dr) at R_i, i.e. the
-    inner-wall Nusselt number -R_i/(H dT) sum dT/dr times ln(R_o / R_i);
-    1 for pure conduction."""
-    r0 = params["r0"]
-    return nu_inner * math.log((r0 + params["nr"]) / r0)
-
-
 def taylor_couette(R_o: int = 50, beta: float = 0.5, kappa: float = 0.1, tau: float = 0.6,
                    Re: float = 5.0, nz: int = 3) -> Case:
     """Circular Couette flow between rotating cylinders (Sec. 3.1).
@@ -288,6 +279,48 @@ def porous_annulus(nr: int = 16, ratio: float = 2.0, Q: float = 0.02, nu: float 
               "T0": 0.5 * (T_in + T_out), "rho0": 1.0, "omega3": 1.0, "omega_hi": 1.0,
               "body_fx": G, "sides": sides}
     return Case("porous_annulus", params, rest_fields(nz, nr, 0.5 * (T_in + T_out)))
+
+
+def rotating_cylinder(R: int = 16, nz: int = 32, u_wall: float = 1e-3, tau: float = 0.8) -> Case:
+    """Closed cylinder turning as a rigid body: the bottom, the lid and the
+    side wall rotate at Omega = u_wall / R, axis of symmetry at r = 0, no
+    heating.  Steady solution of Eq. 1: u_theta = Omega r, no meridian flow,
+    and a radial pressure gradient c^2 d rho / d r = rho Omega^2 r balancing
+    the centrifugal term psi^2 / (rho r) of Eq. 4c."""
+    nu = (tau - 0.5) / 3.0
+    om = u_wall / R
+    sides = [_side(heat=SC_NEUMANN, omega=om), _side(heat=SC_NEUMANN, omega=om), _axis(),
+             _side(heat=SC_NEUMANN, omega=om)]
+    params = {"nr": R, "nz": nz, "r0": 0.0, "nu": nu, "alpha": nu, "g_beta": 0.0, "T0": 0.0,
+              "rho0": 1.0, "omega3": 1.0, "omega_hi": 1.0, "sides": sides, "omega_wall": om}
+    return Case("rotating_cylinder", params, rest_fields(nz, R, 0.0))
+
+
+def axial_couette(nr: int = 16, ratio: float = 2.0, U: float = 1e-3, tau: float = 0.8, nz: int = 3) -> Case:
+    """Annulus whose inner cylinder slides along the axis at speed U, outer
+    cylinder at rest, periodic along z.  Steady solution of Eq. 1b:
+    u_z = U ln(r / R_o) / ln(R_i / R_o), no radial or azimuthal flow."""
+    r0 = nr / (ratio - 1.0)
+    nu = (tau - 0.5) / 3.0
+    sides = [_periodic(), _periodic(), _side(heat=SC_NEUMANN, u_wx=U), _side(heat=SC_NEUMANN)]
+    params = {"nr": nr, "nz": nz, "r0": r0, "nu": nu, "alpha": nu, "g_beta": 0.0, "T0": 0.0,
+              "rho0": 1.0, "omega3": 1.0, "omega_hi": 1.0, "sides": sides, "U": U}
+    return Case("axial_couette", params, rest_fields(nz, nr, 0.0))
+
+
+def couette_zero_flux_outer(nr: int = 16, ratio: float = 2.0, u_inner: float = 1e-3, tau: float = 0.8,
+                            nz: int = 3) -> Case:
+    """Annulus with a rotating inner cylinder (u_theta(R_i) = u_inner) and a
+    zero-flux condition on psi at the outer wall, periodic along z.  Steady
+    solution: u_theta = A r + B / r with d u_theta / d r = A - B / R_o^2 = 0
+    at R_o, i.e. A = u_inner R_i / (R_i^2 + R_o^2), B = A R_o^2."""
+    r0 = nr / (ratio - 1.0)
+    nu = (tau - 0.5) / 3.0
+    sides = [_periodic(), _periodic(), _side(heat=SC_NEUMANN, omega=u_inner / r0),
+             _side(heat=SC_NEUMANN, swirl=SC_NEUMANN)]
+    params = {"nr": nr, "nz": nz, "r0": r0, "nu": nu, "alpha": nu, "g_beta": 0.0, "T0": 0.0,
+              "rho0": 1.0, "omega3": 1.0, "omega_hi": 1.0, "sides": sides, "u_inner": u_inner}
+    return Case("couette_zero_flux_outer", params, rest_fields(nz, nr, 0.0))
 
 
 def annular_conduction(nr: int = 16, ratio: float = 2.0, alpha: float = 0.1, nz: int = 3,

@@ -48,7 +48,8 @@ def test_struct_layouts_match_the_header(tmp_path):
 #include "lb.h"
 int main(void) {
   printf("%zu %zu %zu %zu\\n", sizeof(lb_grid_desc), sizeof(lb_side), sizeof(lb_params), sizeof(lb_diag));
-  printf("%zu %zu %zu\\n", offsetof(lb_params, side), offsetof(lb_diag, step), offsetof(lb_diag, status));
+  printf("%zu %zu %zu %zu\\n", offsetof(lb_params, side), offsetof(lb_diag, step), offsetof(lb_diag, status),
+         offsetof(lb_diag, k_eq_i));
   return 0; }
 """)
     exe = tmp_path / "sz"
@@ -58,7 +59,8 @@ int main(void) {
     offs = list(map(int, b.split()))
     assert sizes == [C.sizeof(_abi.lb_grid_desc), C.sizeof(_abi.lb_side), C.sizeof(_abi.lb_params),
                      C.sizeof(_abi.lb_diag)]
-    assert offs == [_abi.lb_params.side.offset, _abi.lb_diag.step.offset, _abi.lb_diag.status.offset]
+    assert offs == [_abi.lb_params.side.offset, _abi.lb_diag.step.offset, _abi.lb_diag.status.offset,
+                    _abi.lb_diag.k_eq_i.offset]
 
 
 def test_required_bytes_and_argument_checks(lib):

@@ -13,6 +13,16 @@ bounce-back, anti-bounce-back, porous-wall, axis and periodic rules:
   u_theta = A r^(1+Q/nu) + B/r, T = C r^(Q/alpha) + D,
   u_z = -G r^2/(2(2 nu - Q)) + E r^(Q/nu) + F                 -> M^A, F^A_y, S_psi, S_phi
                                                                   with radial flow
+* rigid rotation of a closed cylinder with the axis: u_theta = Omega r exactly
+  up to the O(Ma^2) compressibility of the scheme                -> psi on
+  rotating end walls (column radius), psi and u_theta odd across the axis,
+  psi^2/(rho r) in F_y^A with the axis
+* axial Couette flow, inner cylinder sliding at U:
+  u_z = U ln(r/R_o) / ln(R_i/R_o)                             -> tangential
+  moving-wall term, viscous F_x^A, sliding-wall ghost of u_z
+* rotating inner cylinder, zero-flux psi outer wall:
+  u_theta = A r + B/r, A - B/R_o^2 = 0                        -> psi Neumann
+  rule and its u_theta ghost
 * mass: conserved to round-off without geometric sources; with them the
   mass budget closes (Eq. 23) and the radius-weighted mass is conserved to
   truncation error.
@@ -154,16 +164,23 @@ def test_annular_conduction_profile_and_nusselt():
         exact = np.log(r / Ro) / np.log(Ri / Ro)
         errs.append(rel_l2(fl[4, 1], exact))
         d = o.diag()
-        nus.append((d["nu_i"], d["nu_o"]))
+        nus.append((d["nu_i"], d["nu_o"], d["k_eq_i"], d["k_eq_o"]))
     p = order(errs)
     assert min(p) > 1.7, (errs, p)
     nu_exact = 1.0 / math.log(2.0)
-    ni, no = nus[-1]
+    ni, no, ki, ko = nus[-1]
     assert ni == pytest.approx(nu_exact, rel=5e-3)
     assert no == pytest.approx(nu_exact, rel=5e-3)
+    # the mean equivalent conductivity (Sec. 3.5) of pure conduction is 1 on
+    # both walls: the conducted heat over that of conduction
+    assert ki == pytest.approx(1.0, rel=5e-3)
+    assert ko == pytest.approx(1.0, rel=5e-3)
     for side in (0, 1):
         e_nu = [abs(v[side] - nu_exact) for v in nus]
         assert min(order(e_nu)) > 0.8, e_nu
+    for side in (2, 3):
+        e_k = [abs(v[side] - 1.0) for v in nus]
+        assert min(order(e_k)) > 0.8, e_k
 
 
 def test_cylinder_conduction_linear_profile_and_unit_nusselt():
@@ -220,6 +237,95 @@ def test_porous_annulus_second_order():
         p = order(e)
         assert e[-1] < 5e-3, (k, e)
         assert min(p) > 1.6, (k, e, p)
+
+
+# ---- rotating end walls, the axis and sliding walls (Sec. 3.1, 3.3, 3.4) --------
+
+def _run_for(case, steps):
+    o = oracle.Oracle(case.params)
+    o.init_fields(case.fields)
+    o.step(steps)
+    return o, o.fields()
+
+
+def test_rigid_rotation_of_a_closed_cylinder_is_exact_to_compressibility():
+    """Bottom, lid and side wall turning at Omega about the axis (Sec. 3.4
+    rotating lid, Sec. 3.3 axis mirror): u_theta = Omega r everywhere, with
+    psi_w = rho0 Omega y_j on the end walls, psi odd across the axis and the
+    u_theta ghost odd there.  The scheme reproduces the linear profile
+    exactly; what remains is the O(Ma^2) compressibility of the D2Q5 psi
+    equation (nu lap(rho u_theta) instead of div(rho nu grad u_theta)), so the
+    error falls 100-fold when the wall speed falls 10-fold and does not
+    depend on the grid.  Using the wall radius, or y_j +- 1/2, for psi_w on
+    an end wall gives errors of order 1/R instead."""
+    errs = {}
+    for u in (1e-2, 1e-3):
+        for R in (8, 16):
+            c = W.rotating_cylinder(R=R, nz=2 * R, u_wall=u)
+            o, fl = _run_for(c, 30 * R * R)
+            r = W.radii(R, 0.0)
+            exact = np.broadcast_to(c.params["omega_wall"] * r, fl[3].shape)
+            errs[u, R] = rel_l2(fl[3], exact)
+            # the meridian flow is of second order in the wall speed too
+            assert np.max(np.abs(fl[1:3])) < 1e-3 * u * (u / 1e-2), (u, R)
+    for R in (8, 16):
+        assert errs[1e-3, R] < 1e-6, errs
+        assert errs[1e-2, R] / errs[1e-3, R] == pytest.approx(100.0, rel=0.02), errs
+    assert errs[1e-3, 16] / errs[1e-3, 8] == pytest.approx(1.0, rel=0.1), errs
+
+
+def test_rigid_rotation_radial_pressure_balance_with_the_axis():
+    """c^2 d rho / dr = rho Omega^2 r (Eq. 1c at rest): the centrifugal term
+    psi^2 / (rho y) of F_y^A (Eq. 4c), taken through the axis."""
+    R = 16
+    c = W.rotating_cylinder(R=R, nz=2 * R, u_wall=1e-2)
+    o, fl = _run_for(c, 30 * R * R)
+    om = c.params["omega_wall"]
+    r = W.radii(R, 0.0)
+    rho = fl[0, R]  # mid-height row
+    dpdr = (rho[2:] - rho[:-2]) / 2.0 / 3.0
+    want = rho[1:-1] * om * om * r[1:-1]
+    assert rel_l2(dpdr, want) < 0.03
+
+
+def test_axial_couette_flow_second_order():
+    """Inner cylinder sliding along the axis at U, outer at rest, periodic in
+    z: u_z = U ln(r/R_o) / ln(R_i/R_o).  Pins the tangential part of the
+    moving-wall term 2 w_a rho0 (e_a . u_w) / c^2 together with the viscous
+    force mu (d_x u_y + d_y u_x) / y of Eq. 4b and the wall ghost 2 u_w - u_1
+    of the central differences."""
+    errs = []
+    for nr in (8, 16, 32):
+        c = W.axial_couette(nr=nr, ratio=2.0, U=1e-3)
+        o, fl = run_steady(c, tol=1e-12)
+        Ri = c.params["r0"]
+        Ro = Ri + nr
+        r = W.radii(nr, Ri)
+        exact = c.params["U"] * np.log(r / Ro) / np.log(Ri / Ro)
+        errs.append(rel_l2(fl[1, 1], exact))
+        assert np.max(np.abs(fl[2:4])) < 1e-12
+    p = order(errs)
+    assert errs[-1] < 5e-4, errs
+    assert min(p) > 1.8, (errs, p)
+
+
+def test_couette_with_zero_flux_psi_outer_wall_second_order():
+    """Rotating inner cylinder, zero-flux (bounce-back) psi at the outer wall:
+    u_theta = A r + B / r with u_theta(R_i) = u_i and A - B / R_o^2 = 0.
+    Pins the psi Neumann rule and the zero-gradient u_theta ghost."""
+    errs = []
+    for nr in (8, 16, 32):
+        c = W.couette_zero_flux_outer(nr=nr, ratio=2.0, u_inner=1e-3)
+        o, fl = run_steady(c, tol=1e-12)
+        Ri = c.params["r0"]
+        Ro = Ri + nr
+        r = W.radii(nr, Ri)
+        A = c.params["u_inner"] * Ri / (Ri**2 + Ro**2)
+        exact = A * r + A * Ro**2 / r
+        errs.append(rel_l2(fl[3, 1], exact))
+    p = order(errs)
+    assert errs[-1] < 2e-4, errs
+    assert min(p) > 1.8, (errs, p)
 
 
 # ---- mass ---------------------------------------------------------------------
