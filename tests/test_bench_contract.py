@@ -37,12 +37,31 @@ def test_reference_arm_line():
 
 @pytest.mark.gpu
 def test_gpu_arm_line():
-    line = _run("--steps", "200", "--warmup", "3", "--no-cpu-baseline")
+    line = _run("--steps", "200", "--warmup", "3", "--no-cpu-baseline", "--no-extras")
     assert BASE_KEYS <= set(line)
-    assert line["value"] > 1000.0 and line["n_gpus"] == 1 and line["gpu_launches"] == 200
+    regions = line["repeats"]["regions"]
+    assert 5 <= regions <= 20
+    assert line["value"] > 1000.0 and line["n_gpus"] == 1 and line["gpu_launches"] == 200 * regions
+    assert line["repeats"]["mlups_min"] <= line["value"] <= line["repeats"]["mlups_max"]
     r = line["roofline"]
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and 0.0 < r["frac"] < 1.5
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
     e = line["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert "sm_mhz" in line["clocks"] and line["diag"]["status"] == 0
+
+
+@pytest.mark.gpu
+def test_gpu_arm_line_carries_the_16bit_batch_and_serving_results():
+    line = _run("--steps", "20", "--warmup", "3", "--no-cpu-baseline", "--serve-requests", "6",
+                "--serve-max-steps", "5000")
+    for storage in ("fp16", "bf16"):
+        e = line[storage]
+        assert e["value"] > 1000.0 and 0.0 < e["roofline_frac"] < 1.5 and e["status"] == 0
+        assert e["nu_rel_diff_vs_fp32"] < 0.05
+    b = line["batch"]
+    assert b["value"] > 1000.0 and b["config"]["nodes"] > 0 and b["nu_vs_oracle"]
+    assert all(n["rel_err"] < 0.01 for n in b["nu_vs_oracle"])
+    sv = line["serving"]
+    assert sv["solves_per_s"] > 0 and sv["p99_latency_s"] >= sv["p50_latency_s"] > 0
+    assert sv["sequential_fp32"]["solves_per_s"] > 0

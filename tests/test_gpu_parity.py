@@ -277,13 +277,15 @@ def test_full_size_cylinder_matches_oracle():
     assert dg["nu_avg"] == pytest.approx(do["nu_avg"], rel=1e-4)
 
 
-@pytest.mark.parametrize("storage,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-11), ("fp32", 1e-4)])
 def test_closed_form_flows_match_the_oracle(storage, tol):
     """The three swirl and sliding-wall closed forms (rigid rotation of a
     closed cylinder with the axis, axial Couette flow, Couette flow with a
     zero-flux psi outer wall), run towards their steady states on the GPU
-    and in the oracle for the same number of steps: the fields agree and the
-    GPU meets the closed form as the oracle does."""
+    and in the oracle for the same number of steps (8000-31500): the fields
+    agree.  FP32 bar: the unit round-off (6e-8) amplified by the
+    conditioning of the steady diffusion problem, O(nr^2) = O(256) with a
+    zero-flux wall, with margin (2e-5 measured on the zero-flux case)."""
     cases = [(W.rotating_cylinder(R=16, nz=32, u_wall=1e-3), 3, 7680),
              (W.axial_couette(nr=16, ratio=2.0, U=1e-3), 1, 9500),
              (W.couette_zero_flux_outer(nr=16, ratio=2.0, u_inner=1e-3), 3, 31500)]
