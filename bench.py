@@ -308,7 +308,8 @@ def batch_measure(instances, lo, hi, storage, steps, warmup, graph_steps, oracle
                                    "R_o/R_i ~ U[1.5,3], Ra log-U[1e3,1e5], inner swirl ~ U[0,0.05], seeds 0..",
                        "nodes": nodes, "storage": storage,
                        "launch": {"seg_rows": launch[0], "warps_per_block": launch[1], "row_fetch": launch[2],
-                                  "graph_steps": graph_steps},
+                                  "graph_steps": graph_steps,
+                                  "segment_plan_waves": launch[3]},
                        "l2": ("inputs larger than L2 (working set %.0f MB)" % (bpn * nodes / 1e6)
                               if bpn * nodes > L2_BYTES else
                               "working set %.0f MB fits in the L2: an L2-resident rate" % (bpn * nodes / 1e6))},

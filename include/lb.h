@@ -269,9 +269,24 @@ LB_EXPORT lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_bu
 /* rows per z-segment (0 = keep), warps per block (0 = keep), launches per
  * CUDA graph (0 or 1 = no graph), row fetch (0 = keep, 1 = plain loads on a
  * persistent grid, 3 = TMA ring read in place, one warp per work item; the
- * default is 3).  LB_ERR_ARG for values out of range. */
+ * default is 3; 4 = the same with a ring of three row stages instead of
+ * four, FP32 storage only: 12 instead of 10 resident warps per SM, for
+ * batches whose step is one wave of work items).  LB_ERR_ARG for values out
+ * of range. */
 LB_EXPORT lb_status lb_batch_set_launch(lb_batch *b, int32_t seg_rows, int32_t warps_per_block,
                                         int32_t graph_steps, int32_t row_fetch);
+/* Rows per z-segment of each lattice (seg_rows[n], in the order of
+ * lb_batch_create; 0 = the batch's common value from lb_batch_set_launch;
+ * NULL resets every lattice to it), so that the work items of uneven
+ * lattices can be sized per lattice -- e.g. about the same number of rows
+ * in every item, and items that fill whole waves of the resident warps.
+ * Results do not depend on the segments.  LB_ERR_ARG for a value outside
+ * 0..nz. */
+LB_EXPORT lb_status lb_batch_set_segments(lb_batch *b, const int32_t *seg_rows);
+/* Warps of the batched step that can be resident on the device at once
+ * under the current launch, and the number of work items (64-column window x
+ * z-segment) of one step.  NULL outputs are skipped. */
+LB_EXPORT lb_status lb_batch_get_occupancy(const lb_batch *b, int32_t *resident_warps, int32_t *items);
 LB_EXPORT lb_status lb_batch_step(lb_batch *b, int32_t nsteps);
 /* lb_diagnostics of every lattice of the batch (out[n], in the order of
  * lb_batch_create), bitwise equal to lb_diagnostics of each lattice: three

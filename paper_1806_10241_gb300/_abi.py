@@ -75,6 +75,8 @@ PROTOTYPES = {
     "lb_batch_set_launch": (_st, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "lb_selftest_timeout": (_st, [_vp, C.c_int32]),
     "lb_stream_function": (_st, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "lb_batch_set_segments": (_st, [_vp, C.POINTER(C.c_int32)]),
+    "lb_batch_get_occupancy": (_st, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "lb_batch_step": (_st, [_vp, C.c_int32]),
     "lb_batch_diagnostics": (_st, [_vp, _vp]),
     "lb_batch_destroy": (_st, [_vp]),

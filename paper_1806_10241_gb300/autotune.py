@@ -5,6 +5,11 @@ CUDA events on the solver's own stream for a few steps each; the steps taken
 while tuning are real time steps (results do not depend on the launch shape).
 The best shape is applied and remembered in a JSON cache keyed by storage and
 lattice size class.
+
+For a batch of uneven lattices the candidates also include per-lattice
+segment plans: every lattice's z-segments sized so that all work items hold
+about the same number of rows and the items fill a chosen number of waves
+of the warps that can be resident at once (segment_plan).
 """
 from __future__ import annotations
 
@@ -76,25 +81,60 @@ def tune_solver(solver, steps: int = 20, use_cache: bool = True) -> tuple:
     return best
 
 
+PLAN_WAVES = [1.0, 1.5, 2.0, 3.0, 4.0, 6.0]
+
+
+def segment_plan(shapes: list, resident: int, waves: float, window: int = 64) -> list:
+    """Rows per z-segment for each lattice (nr, nz) of a batch: the step's
+    warp-rows (window-column windows x rows, summed over the lattices) split
+    into about `waves` x `resident` work items of equal length, each lattice's
+    rows cut into that many balanced segments."""
+    warp_rows = sum(-(-nr // window) * nz for nr, nz in shapes)
+    rows = max(1.0, warp_rows / max(1.0, waves * resident))
+    plan = []
+    for nr, nz in shapes:
+        nseg = max(1, int(round(nz / rows)))
+        plan.append(-(-nz // nseg))
+    return plan
+
+
+def _apply(batch, launch, waves, graph_steps):
+    seg, wpb, fetch = launch
+    batch.set_launch(seg, wpb, graph_steps, fetch)
+    if waves:
+        resident, _ = batch.occupancy()
+        batch.set_segments(segment_plan([(s.nr, s.nz) for s in batch.solvers], resident, waves))
+    else:
+        batch.set_segments(None)
+
+
 def tune_batch(batch, steps: int = 10, graph_steps: int = 10, use_cache: bool = True) -> tuple:
-    """Pick (seg_rows, warps_per_block, row_fetch) for a batch, keyed by its node count."""
+    """Pick the batch's launch: (seg_rows, warps_per_block, row_fetch) for
+    every lattice, or a per-lattice segment plan (segment_plan) for a number
+    of waves, with the TMA-ring step; keyed by storage, node count and
+    lattice count.  Returns (seg_rows, warps_per_block, row_fetch, waves),
+    waves = 0 for a common segment length."""
     key = f"batch/{batch.solvers[0].storage}/{_size_class(batch.nodes)}/{_size_class(len(batch.solvers))}"
     with _lock:
         cache = _load() if use_cache else {}
-    if key in cache and len(cache[key]["launch"]) == 3:
-        best = tuple(cache[key]["launch"])
-        batch.set_launch(best[0], best[1], graph_steps, best[2])
+    if key in cache and len(cache[key].get("launch", [])) == 3 and "waves" in cache[key]:
+        best = tuple(cache[key]["launch"]) + (cache[key]["waves"],)
+        _apply(batch, best[:3], best[3], graph_steps)
         return best
+    plan_launches = [(4, 1, 3), (4, 2, 3)]
+    if batch.solvers[0].storage == "fp32":  # three ring stages: 12 resident warps per SM instead of 10
+        plan_launches += [(4, 1, 4), (4, 2, 4)]
+    cands = [(c, 0.0) for c in BATCH_CANDIDATES] + [(c, w) for c in plan_launches for w in PLAN_WAVES]
     results = []
-    for seg, wpb, fetch in BATCH_CANDIDATES:
-        batch.set_launch(seg, wpb, 0, fetch)
+    for launch, waves in cands:
+        _apply(batch, launch, waves, 0)
         batch.step(2)
-        results.append((_time(batch.stream, batch.step, steps), (seg, wpb, fetch)))
-    results.sort()
-    best = results[0][1]
-    batch.set_launch(best[0], best[1], graph_steps, best[2])
+        results.append((_time(batch.stream, batch.step, steps), launch, waves))
+    results.sort(key=lambda r: r[0])
+    _, launch, waves = results[0]
+    _apply(batch, launch, waves, graph_steps)
     with _lock:
         cache = _load()
-        cache[key] = {"launch": list(best), "ms_per_step": results[0][0]}
+        cache[key] = {"launch": list(launch), "waves": waves, "ms_per_step": results[0][0]}
         _store(cache)
-    return best
+    return tuple(launch) + (waves,)

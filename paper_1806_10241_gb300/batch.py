@@ -35,9 +35,27 @@ class Batch:
 
     def set_launch(self, seg_rows: int = 0, warps_per_block: int = 0, graph_steps: int = 8,
                    row_fetch: int = 0) -> None:
-        """row_fetch: 0 keep, 1 plain loads, 3 TMA ring read in place."""
+        """row_fetch: 0 keep, 1 plain loads, 3 TMA ring read in place, 4 the
+        same with three ring stages (FP32)."""
         _abi.check(self.L.lb_batch_set_launch(self.h, int(seg_rows), int(warps_per_block), int(graph_steps),
                                               int(row_fetch)))
+
+    def set_segments(self, seg_rows: list | None) -> None:
+        """Rows per z-segment of each lattice (0: the common value; None:
+        every lattice back to the common value)."""
+        if seg_rows is None:
+            _abi.check(self.L.lb_batch_set_segments(self.h, None))
+            return
+        if len(seg_rows) != len(self.solvers):
+            raise ValueError("one value per lattice")
+        arr = (C.c_int32 * len(seg_rows))(*[int(v) for v in seg_rows])
+        _abi.check(self.L.lb_batch_set_segments(self.h, arr))
+
+    def occupancy(self) -> tuple:
+        """(resident warps of the batched step, work items of one step)."""
+        r, n = C.c_int32(), C.c_int32()
+        _abi.check(self.L.lb_batch_get_occupancy(self.h, C.byref(r), C.byref(n)))
+        return r.value, n.value
 
     def step(self, n: int = 1) -> None:
         _abi.check(self.L.lb_batch_step(self.h, int(n)))

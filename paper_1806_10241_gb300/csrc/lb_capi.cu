@@ -613,6 +613,7 @@ struct lb_batch {
     std::vector<char> hdiag;
     cudaStream_t stream;
     int seg_rows, wpb, blocks, total, graph_steps, row_fetch;
+    std::vector<int> seg_of;             // per lattice rows per z-segment (0: seg_rows)
     unsigned long long counter;
     cudaGraphExec_t gexec;
     bool graph_valid;
@@ -671,10 +672,13 @@ static lb_status batch_upload(lb_batch *b)
     b->hprefix.assign((size_t)n + 1, 0);
     for (int m = 0; m < n; ++m) {
         lb_ctx *c = b->ctxs[m];
-        cudaError_t e = lbk::batch_fill_desc(c->hp, c->dist[0], c->dist[1], b->step0[m], b->parity0[m],
-                                             b->seg_rows, c->status, b->hdesc.data() + (size_t)m * db);
+        const int seg = b->seg_of[m] ? b->seg_of[m] : b->seg_rows;
+        cudaError_t e = lbk::batch_fill_desc(c->hp, c->dist[0], c->dist[1], b->step0[m], b->parity0[m], seg,
+                                             c->status, b->hdesc.data() + (size_t)m * db);
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch descriptor (tensor map)");
-        b->hprefix[m + 1] = b->hprefix[m] + lbk::batch_items(c->hp, b->seg_rows);
+        const long long items = (long long)b->hprefix[m] + lbk::batch_items(c->hp, seg);
+        if (items > (1LL << 30)) return fail(nullptr, LB_ERR_ARG, "too many work items in the batch");
+        b->hprefix[m + 1] = (int)items;
     }
     b->total = b->hprefix[n];
     cudaError_t e = cudaMemcpyAsync(b->d_desc, b->hdesc.data(), b->hdesc.size(), cudaMemcpyHostToDevice, b->stream);
@@ -735,6 +739,7 @@ lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_buf, size_t 
     b->bdiag_uploaded = false;
     b->stream = (cudaStream_t)cuda_stream;
     b->seg_rows = 4;
+    b->seg_of.assign((size_t)n, 0);
     b->wpb = 1;
     b->graph_steps = 8;
     b->row_fetch = 3;
@@ -769,9 +774,11 @@ lb_status lb_batch_set_launch(lb_batch *b, int32_t seg_rows, int32_t warps_per_b
                               int32_t row_fetch)
 {
     if (!b || seg_rows < 0 || warps_per_block < 0 || warps_per_block > 8 || graph_steps < 0 ||
-        !(row_fetch == 0 || row_fetch == 1 || row_fetch == 3))
+        !(row_fetch == 0 || row_fetch == 1 || row_fetch == 3 || row_fetch == 4))
         return fail(nullptr, LB_ERR_ARG,
-                    "seg_rows >= 0, 0 <= warps_per_block <= 8, graph_steps >= 0, row_fetch 0, 1 or 3");
+                    "seg_rows >= 0, 0 <= warps_per_block <= 8, graph_steps >= 0, row_fetch 0, 1, 3 or 4");
+    if (row_fetch == 4 && b->storage != LB_FP32)
+        return fail(nullptr, LB_ERR_ARG, "row_fetch 4 (three ring stages) is for FP32 storage");
     if (row_fetch) b->row_fetch = row_fetch;
     if (seg_rows) b->seg_rows = seg_rows;
     if (warps_per_block) {
@@ -780,6 +787,31 @@ lb_status lb_batch_set_launch(lb_batch *b, int32_t seg_rows, int32_t warps_per_b
     }
     b->graph_steps = graph_steps;
     return batch_upload(b);
+}
+
+lb_status lb_batch_set_segments(lb_batch *b, const int32_t *seg_rows)
+{
+    if (!b) return fail(nullptr, LB_ERR_ARG, "batch is NULL");
+    const int n = (int)b->ctxs.size();
+    if (seg_rows)
+        for (int m = 0; m < n; ++m)
+            if (seg_rows[m] < 0 || seg_rows[m] > b->ctxs[m]->hp.nz)
+                return fail(nullptr, LB_ERR_ARG, "lattice %d: rows per z-segment must lie in 0..nz", m);
+    for (int m = 0; m < n; ++m) b->seg_of[m] = seg_rows ? seg_rows[m] : 0;
+    return batch_upload(b);
+}
+
+lb_status lb_batch_get_occupancy(const lb_batch *b, int32_t *resident_warps, int32_t *items)
+{
+    if (!b) return fail(nullptr, LB_ERR_ARG, "batch is NULL");
+    if (resident_warps) {
+        int r = 0;
+        cudaError_t e = lbk::batch_resident_warps(b->storage, b->row_fetch, b->wpb, &r);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "occupancy");
+        *resident_warps = r;
+    }
+    if (items) *items = b->total;
+    return LB_OK;
 }
 
 lb_status lb_batch_step(lb_batch *b, int32_t nsteps)

@@ -103,6 +103,9 @@ int batch_items(const HostParams &h, int seg_rows);
 cudaError_t batch_fill_desc(const HostParams &h, void *buf0, void *buf1, unsigned long long step0, int parity0,
                             int seg_rows, int *status, void *out);
 int batch_grid(int storage, int wpb);
+// Warps of the batched step (row_fetch 1 or 3, wpb warps per block) that can
+// be resident on the device at once.
+cudaError_t batch_resident_warps(int storage, int row_fetch, int wpb, int *out);
 // Kernel attributes of the batched step; called before any stream capture.
 cudaError_t batch_prepare(int storage);
 // row_fetch: 1 plain loads (persistent grid of `blocks`), 3 TMA ring read in

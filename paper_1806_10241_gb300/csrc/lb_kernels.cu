@@ -1246,30 +1246,33 @@ __global__ void __maxnreg__(LB_STEP2_MAXREG) k_batch(const BatchDesc *__restrict
 // multiple of 128 bytes), then one KP per warp.  Each stage's mbarrier sits in
 // the padding after the stage's box, which the copies never write, so that
 // ten FP32 warps still fit on an SM (22,272 bytes per warp).
-template <typename S>
+// R ring stages per warp: 4 by default (one more row in flight); 3 in the
+// FP32 variant that fits 12 instead of 10 warps on an SM (16.9 instead of
+// 22.3 KB of shared memory per warp), for batches too small to fill the GPU,
+// whose step time is the latency of one wave of work items.
+template <typename S, int R>
 __host__ __device__ constexpr size_t batch3_ring_bytes()
 {
     static_assert(TmaGeom<S>::stage_bytes - TmaGeom<S>::box_bytes >= 8 && TmaGeom<S>::box_bytes % 8 == 0,
                   "room for the stage's mbarrier after its box");
-    return (size_t)kRingStages<S> * TmaGeom<S>::stage_bytes;
+    return (size_t)R * TmaGeom<S>::stage_bytes;
 }
-template <typename S>
+template <typename S, int R = kRingStages<S>>
 __host__ __device__ size_t batch3_smem_bytes(int wpb)
 {
-    return (size_t)wpb * (batch3_ring_bytes<S>() + sizeof(KP<float>));
+    return (size_t)wpb * (batch3_ring_bytes<S, R>() + sizeof(KP<float>));
 }
 
-template <typename S>
+template <typename S, int R>
 __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restrict__ d, const int *__restrict__ prefix,
                                                       int n, int total, const BatchCtl *ctl, unsigned long long t0,
                                                       int from_counter)
 {
-    constexpr int R = kRingStages<S>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
-    unsigned char *ring = smem + batch3_ring_bytes<S>() * wib;
-    KP<float> *skp = reinterpret_cast<KP<float> *>(smem + batch3_ring_bytes<S>() * wpb);
+    unsigned char *ring = smem + batch3_ring_bytes<S, R>() * wib;
+    KP<float> *skp = reinterpret_cast<KP<float> *>(smem + batch3_ring_bytes<S, R>() * wpb);
     // Programmatic dependent launch: the next step's blocks may become
     // resident now.  The instance lookup and the parameter copy read only
     // what no launch of the batch writes (the prefix sums, the descriptors),
@@ -1693,14 +1696,18 @@ cudaError_t batch_fill_desc(const HostParams &h, void *buf0, void *buf1, unsigne
 cudaError_t batch_prepare(int storage)
 {
     switch (storage) {
-        case ST_FP32:
-            return cudaFuncSetAttribute(k_batch3<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)batch3_smem_bytes<float>(8));
+        case ST_FP32: {
+            cudaError_t e = cudaFuncSetAttribute(k_batch3<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)batch3_smem_bytes<float, 4>(8));
+            if (e != cudaSuccess) return e;
+            return cudaFuncSetAttribute(k_batch3<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)batch3_smem_bytes<float, 3>(8));
+        }
         case ST_FP16:
-            return cudaFuncSetAttribute(k_batch3<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            return cudaFuncSetAttribute(k_batch3<__half, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)batch3_smem_bytes<__half>(8));
         case ST_BF16:
-            return cudaFuncSetAttribute(k_batch3<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            return cudaFuncSetAttribute(k_batch3<__nv_bfloat16, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)batch3_smem_bytes<__nv_bfloat16>(8));
         default: return cudaErrorInvalidValue;
     }
@@ -1721,6 +1728,40 @@ int batch_grid(int storage, int wpb)
     return sms * (per > 0 ? per : 1);
 }
 
+cudaError_t batch_resident_warps(int storage, int row_fetch, int wpb, int *out)
+{
+    if (row_fetch == 1) {
+        *out = batch_grid(storage, wpb) * wpb;
+        return cudaSuccess;
+    }
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = batch_prepare(storage);
+    if (e != cudaSuccess) return e;
+    switch (storage) {
+        case ST_FP32:
+            if (row_fetch == 4)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch3<float, 3>, 32 * wpb,
+                                                                  batch3_smem_bytes<float, 3>(wpb));
+            else
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch3<float, 4>, 32 * wpb,
+                                                                  batch3_smem_bytes<float, 4>(wpb));
+            break;
+        case ST_FP16:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch3<__half, 4>, 32 * wpb,
+                                                              batch3_smem_bytes<__half>(wpb));
+            break;
+        case ST_BF16:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch3<__nv_bfloat16, 4>, 32 * wpb,
+                                                              batch3_smem_bytes<__nv_bfloat16>(wpb));
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    *out = sms * per * wpb;
+    return e;
+}
+
 cudaError_t launch_batch_counter(void *ctl, unsigned long long value, int add, cudaStream_t s)
 {
     k_batch_counter<<<1, 32, 0, s>>>((BatchCtl *)ctl, value, add);
@@ -1734,19 +1775,23 @@ cudaError_t launch_batch(int storage, int row_fetch, const void *desc, const int
     if (need < 1) return cudaSuccess;
     const BatchDesc *dd = (const BatchDesc *)desc;
     const BatchCtl *cc = (const BatchCtl *)ctl;
-    if (row_fetch == 3) {
+    if (row_fetch == 3 || row_fetch == 4) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute pdl[1];
         switch (storage) {
             case ST_FP32:
-                pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), batch3_smem_bytes<float>(wpb), s);
-                return cudaLaunchKernelEx(&cfg, k_batch3<float>, dd, prefix, n, total, cc, t0, from_counter);
+                if (row_fetch == 4) {
+                    pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), batch3_smem_bytes<float, 3>(wpb), s);
+                    return cudaLaunchKernelEx(&cfg, k_batch3<float, 3>, dd, prefix, n, total, cc, t0, from_counter);
+                }
+                pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), batch3_smem_bytes<float, 4>(wpb), s);
+                return cudaLaunchKernelEx(&cfg, k_batch3<float, 4>, dd, prefix, n, total, cc, t0, from_counter);
             case ST_FP16:
                 pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), batch3_smem_bytes<__half>(wpb), s);
-                return cudaLaunchKernelEx(&cfg, k_batch3<__half>, dd, prefix, n, total, cc, t0, from_counter);
+                return cudaLaunchKernelEx(&cfg, k_batch3<__half, 4>, dd, prefix, n, total, cc, t0, from_counter);
             case ST_BF16:
                 pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), batch3_smem_bytes<__nv_bfloat16>(wpb), s);
-                return cudaLaunchKernelEx(&cfg, k_batch3<__nv_bfloat16>, dd, prefix, n, total, cc, t0,
+                return cudaLaunchKernelEx(&cfg, k_batch3<__nv_bfloat16, 4>, dd, prefix, n, total, cc, t0,
                                           from_counter);
             default: return cudaErrorInvalidValue;
         }

@@ -40,3 +40,21 @@ def test_cache_survives_a_corrupt_file(tmp_path, monkeypatch):
     assert autotune._load() == {}
     autotune._store({"a": {"launch": [4, 1, 3]}})
     assert autotune._load() == {"a": {"launch": [4, 1, 3]}}
+
+
+def test_segment_plan_balances_items_and_fills_the_waves():
+    """Every lattice's segments differ by at most one row from the common
+    item length, and the item count is close to waves x resident warps."""
+    shapes = [(64 + 7 * m, (64 + 7 * m) * (1 + m % 2)) for m in range(40)]
+    resident = 1520
+    for waves in autotune.PLAN_WAVES:
+        plan = autotune.segment_plan(shapes, resident, waves)
+        assert len(plan) == len(shapes)
+        items = sum(-(-nr // 64) * -(-nz // seg) for (nr, nz), seg in zip(shapes, plan))
+        assert 0.8 * waves * resident <= items <= 1.25 * waves * resident, (waves, items)
+        rows = [nz / -(-nz // seg) for (nr, nz), seg in zip(shapes, plan)]
+        assert max(rows) / min(rows) < 1.6, (waves, min(rows), max(rows))
+        for (nr, nz), seg in zip(shapes, plan):
+            assert 1 <= seg <= nz
+    # one lattice far smaller than the item length keeps a single segment
+    assert autotune.segment_plan([(64, 8), (1024, 2048)], 152, 1.0)[0] == 8

@@ -59,7 +59,8 @@ def test_batch_tuning_is_cached(cache):
         sols.append(s)
     b = Batch(sols, stream=stream)
     best = autotune.tune_batch(b, steps=3, graph_steps=4)
-    assert best in autotune.BATCH_CANDIDATES
+    assert (best[3] == 0 and best[:3] in autotune.BATCH_CANDIDATES) or (
+        best[3] in autotune.PLAN_WAVES and best[2] in (3, 4))
     assert autotune.tune_batch(b, steps=3, graph_steps=4) == best
     b.step(8)
     assert all(d["status"] == 0 for d in b.diag())

@@ -42,7 +42,7 @@ def test_batch_equals_individual_runs(storage, row_fetch):
         s = Solver(c.params, storage=storage, stream=stream)
         s.set_launch(0, 0, row_fetch)
         s.init_fields(c.fields)
-        s.step(37)
+        s.step(49)
         alone.append(s.get_dist())
     mixed = []
     for c in cases:
@@ -56,9 +56,19 @@ def test_batch_equals_individual_runs(storage, row_fetch):
     b.set_launch(seg_rows=3, warps_per_block=2, graph_steps=4, row_fetch=3)
     b.step(11)  # 2 graph replays, then 3 launches outside the graph
     b.step(5)  # 1 replay, 1 launch
+    # per-lattice segments (0: the common value; 31 = the whole height of lattice 3)
+    b.set_segments([1, 7, 2, 31, 0, 3, 11, 3])
+    b.step(6)
+    b.set_segments(None)
+    b.step(1)
+    if storage == "fp32":  # three ring stages
+        b.set_launch(seg_rows=4, warps_per_block=2, graph_steps=4, row_fetch=4)
+        b.step(5)
+    else:
+        b.step(5)
     torch.cuda.synchronize()
     for c, a, s in zip(cases, alone, mixed):
-        assert s.step_count == 37
+        assert s.step_count == 49
         assert np.array_equal(s.get_dist(), a), c.name
     b.close()
 
@@ -153,4 +163,28 @@ def test_batch_diagnostics_follow_a_changed_launch():
     sols[2].set_launch(48, 2, 0)  # 48-row segments: another diagnostics grid
     b.step(3)
     assert b.diag() == [s.diag() for s in sols]
+    b.close()
+
+
+def test_segment_plan_rejects_out_of_range_values():
+    from paper_1806_10241_gb300._abi import LBError
+    from paper_1806_10241_gb300.batch import Batch
+    from paper_1806_10241_gb300.solver import Solver
+    cases = _cases()[:3]
+    sols = []
+    for c in cases:
+        s = Solver(c.params, storage="fp32")
+        s.init_fields(c.fields)
+        sols.append(s)
+    b = Batch(sols, stream=torch.cuda.Stream())
+    with pytest.raises(LBError):
+        b.set_segments([1, -1, 2])
+    with pytest.raises(LBError):
+        b.set_segments([1, cases[1].nz + 1, 2])
+    b.set_launch(row_fetch=4)
+    r4, _ = b.occupancy()
+    b.set_launch(row_fetch=3)
+    resident, items = b.occupancy()
+    assert resident >= 152 and items > 0
+    assert r4 > resident  # three stages: more warps resident
     b.close()
