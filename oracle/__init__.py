@@ -24,8 +24,8 @@ _lock = threading.Lock()
 _lib = None
 
 # side indices: 0 bottom (x=0), 1 top (x=H), 2 inner (y=r0), 3 outer (y=r0+nr)
-FLOW_WALL, FLOW_AXIS, FLOW_PERIODIC = 0, 1, 2
-SC_DIRICHLET, SC_NEUMANN, SC_AXIS, SC_PERIODIC = 0, 1, 2, 3
+FLOW_WALL, FLOW_AXIS, FLOW_PERIODIC, FLOW_FREE = 0, 1, 2, 3
+SC_DIRICHLET, SC_NEUMANN, SC_AXIS, SC_PERIODIC, SC_RAMP = 0, 1, 2, 3, 4
 
 
 class Side(C.Structure):
@@ -41,7 +41,8 @@ class Params(C.Structure):
                 ("omega_hi", C.c_double), ("g_beta", C.c_double), ("T0", C.c_double),
                 ("body_fx", C.c_double), ("rho0", C.c_double), ("planar", C.c_int32),
                 ("sign_literal", C.c_int32), ("explicit_sources", C.c_int32),
-                ("pad", C.c_int32), ("side", Side * 4)]
+                ("pad", C.c_int32), ("side", Side * 4), ("top_split", C.c_int32), ("pad2", C.c_int32),
+                ("top_outer", Side)]
 
 
 class Diag(C.Structure):
@@ -118,14 +119,19 @@ def make_params(d: dict) -> Params:
     p.planar = int(d.get("planar", 0))
     p.sign_literal = int(d.get("sign_literal", 0))
     p.explicit_sources = int(d.get("explicit_sources", 0))
+    def fill(dst, s):
+        dst.flow = int(s.get("flow", FLOW_WALL))
+        dst.swirl = int(s.get("swirl", SC_DIRICHLET))
+        dst.heat = int(s.get("heat", SC_NEUMANN))
+        dst.u_wx = float(s.get("u_wx", 0.0))
+        dst.u_wy = float(s.get("u_wy", 0.0))
+        dst.omega = float(s.get("omega", 0.0))
+        dst.T_w = float(s.get("T_w", 0.0))
     for i, s in enumerate(d["sides"]):
-        p.side[i].flow = int(s.get("flow", FLOW_WALL))
-        p.side[i].swirl = int(s.get("swirl", SC_DIRICHLET))
-        p.side[i].heat = int(s.get("heat", SC_NEUMANN))
-        p.side[i].u_wx = float(s.get("u_wx", 0.0))
-        p.side[i].u_wy = float(s.get("u_wy", 0.0))
-        p.side[i].omega = float(s.get("omega", 0.0))
-        p.side[i].T_w = float(s.get("T_w", 0.0))
+        fill(p.side[i], s)
+    p.top_split = int(d.get("top_split", 0))
+    if "top_outer" in d:
+        fill(p.top_outer, d["top_outer"])
     return p
 
 

@@ -28,7 +28,7 @@ static const int EY5[5] = {0, 0, 1, 0, -1};
 static const double CS2 = 1.0 / 3.0;
 
 /* derived by search over the velocity sets, not tabulated */
-static int OPP9[9], MIRY9[9], OPP5[5];
+static int OPP9[9], MIRY9[9], MIRX9[9], OPP5[5];
 static double W9[9], W5[5];
 static int tables_ready = 0;
 
@@ -39,6 +39,7 @@ static void build_tables(void)
         for (int b = 0; b < 9; ++b) {
             if (EX9[b] == -EX9[a] && EY9[b] == -EY9[a]) OPP9[a] = b;
             if (EX9[b] == EX9[a] && EY9[b] == -EY9[a]) MIRY9[a] = b;
+            if (EX9[b] == -EX9[a] && EY9[b] == EY9[a]) MIRX9[a] = b;
         }
     for (int a = 0; a < 5; ++a)
         for (int b = 0; b < 5; ++b)
@@ -199,10 +200,21 @@ static int valid_params(const orc_params *p)
         if ((p->side[s].heat == ORC_SC_PERIODIC) != per) return 0;
         if (p->side[s].flow == ORC_FLOW_AXIS || p->side[s].swirl == ORC_SC_AXIS ||
             p->side[s].heat == ORC_SC_AXIS) return 0;
+        if (p->side[s].swirl == ORC_SC_RAMP || p->side[s].heat == ORC_SC_RAMP) return 0;
+    }
+    if (p->top_split < 0 || p->top_split >= p->nr) return 0;
+    if (p->top_split > 0) {
+        const orc_side *t = &p->top_outer;
+        if (p->side[1].flow == ORC_FLOW_PERIODIC) return 0;
+        if (t->flow != ORC_FLOW_WALL && t->flow != ORC_FLOW_FREE) return 0;
+        if (t->swirl != ORC_SC_DIRICHLET && t->swirl != ORC_SC_NEUMANN) return 0;
+        if (t->heat != ORC_SC_DIRICHLET && t->heat != ORC_SC_NEUMANN && t->heat != ORC_SC_RAMP) return 0;
     }
     for (int s = 2; s < 4; ++s) {
         if (p->side[s].flow == ORC_FLOW_PERIODIC || p->side[s].swirl == ORC_SC_PERIODIC ||
             p->side[s].heat == ORC_SC_PERIODIC) return 0;
+        if (p->side[s].flow == ORC_FLOW_FREE || p->side[s].swirl == ORC_SC_RAMP ||
+            p->side[s].heat == ORC_SC_RAMP) return 0;
         int ax = p->side[s].flow == ORC_FLOW_AXIS;
         if ((p->side[s].swirl == ORC_SC_AXIS) != ax || (p->side[s].heat == ORC_SC_AXIS) != ax) return 0;
         if (ax && (s != 2 || p->r0 != 0.0)) return 0;
@@ -344,13 +356,35 @@ static void pass0(orc_state *s)
 /* u_theta prescribed by a rotating wall: omega * radius, where the radius is
  * that of the node's column on an end wall (lid, Sec. 3.4) and the cylinder
  * radius on a lateral wall (Sec. 3.1, 3.5).  psi_w = rho0 u_theta. */
+/* The specification of an end wall at column j: the top's outer segment
+ * when the top is split (Sec. 3.6: the crystal inside a free surface), else
+ * the side itself. */
+static const orc_side *end_side(const orc_params *p, int side, int j)
+{
+    if (side == 1 && p->top_split > 0 && j >= p->top_split) return &p->top_outer;
+    return &p->side[side];
+}
+
+/* Wall temperature of an end wall at column j: T_w, or on the top's outer
+ * segment with the ramp of Sec. 3.6 the value linear in r from the inner
+ * segment's T_w at the split radius r0 + top_split to the outer segment's
+ * T_w at r0 + nr, taken at the column's radius. */
+static double end_T(const orc_params *p, int side, int j)
+{
+    const orc_side *sd = end_side(p, side, j);
+    if (sd->heat != ORC_SC_RAMP) return sd->T_w;
+    const double rs = p->r0 + p->top_split, ro = p->r0 + p->nr, y = p->r0 + j + 0.5;
+    return p->side[1].T_w + (y - rs) / (ro - rs) * (sd->T_w - p->side[1].T_w);
+}
+
 static double wall_psi(const orc_params *p, int side, int j)
 {
     double radius;
     if (side <= 1) radius = p->r0 + j + 0.5;
     else if (side == 2) radius = p->r0;
     else radius = p->r0 + p->nr;
-    return p->rho0 * p->side[side].omega * radius;
+    const double omega = side <= 1 ? end_side(p, side, j)->omega : p->side[side].omega;
+    return p->rho0 * omega * radius;
 }
 
 /* f_a(x) = f^p_a(x - e_a), Eq. 16b.  A source outside the fluid is replaced
@@ -360,6 +394,25 @@ static double wall_psi(const orc_params *p, int side, int j)
  * mirror image across the axis (the population
  * with e_y reversed, taken at the mirrored source).  A node whose source
  * crosses both an end wall and the axis uses the end wall. */
+/* A population entering node (i, j) through a free-surface end wall (Sec.
+ * 3.6: no normal velocity, no shear): the specular image of the population
+ * that left node (i, j - e_ay) towards the wall, with e_x reversed.  When
+ * that node lies beyond a lateral side (a corner), the image is taken
+ * across that side too: across the axis the mirror image of the node itself
+ * (both components reversed), at a wall its bounce-back with the wall's
+ * momentum term. */
+static double free_surface_f(const orc_state *s, int i, int j, int a)
+{
+    const orc_params *p = &s->p;
+    const int sj = j - EY9[a];
+    if (sj >= 0 && sj < p->nr) return s->f[9 * NODE(s, i, sj) + MIRX9[a]];
+    const int lat = sj < 0 ? 2 : 3;
+    const double own = s->f[9 * NODE(s, i, j) + OPP9[a]];
+    if (p->side[lat].flow == ORC_FLOW_AXIS) return own;
+    const double eu = EX9[a] * p->side[lat].u_wx + EY9[a] * p->side[lat].u_wy;
+    return own + 2.0 * W9[a] * p->rho0 * eu / CS2;
+}
+
 static double pull_f(const orc_state *s, int i, int j, int a)
 {
     const orc_params *p = &s->p;
@@ -369,7 +422,9 @@ static double pull_f(const orc_state *s, int i, int j, int a)
         if (p->side[side].flow == ORC_FLOW_PERIODIC) {
             si = (si + p->nz) % p->nz;
         } else {
-            const double eu = EX9[a] * p->side[side].u_wx + EY9[a] * p->side[side].u_wy;
+            const orc_side *sd = end_side(p, side, j);
+            if (sd->flow == ORC_FLOW_FREE) return free_surface_f(s, i, j, a);
+            const double eu = EX9[a] * sd->u_wx + EY9[a] * sd->u_wy;
             return s->f[9 * NODE(s, i, j) + OPP9[a]] + 2.0 * W9[a] * p->rho0 * eu / CS2;
         }
     }
@@ -402,10 +457,11 @@ static double pull_s(const orc_state *s, int field, int i, int j, int a)
         side = sj < 0 ? 2 : 3;
     }
     if (side < 0) return arr[5 * NODE(s, si, sj) + a];
-    const int bc = field == 0 ? p->side[side].swirl : p->side[side].heat;
+    const orc_side *sd = side <= 1 ? end_side(p, side, j) : &p->side[side];
+    const int bc = field == 0 ? sd->swirl : sd->heat;
     const double own = arr[5 * NODE(s, i, j) + OPP5[a]];
-    if (bc == ORC_SC_DIRICHLET) {
-        const double val = field == 0 ? wall_psi(p, side, j) : p->side[side].T_w;
+    if (bc == ORC_SC_DIRICHLET || bc == ORC_SC_RAMP) {
+        const double val = field == 0 ? wall_psi(p, side, j) : (side <= 1 ? end_T(p, side, j) : sd->T_w);
         return -own + 2.0 * W5[a] * val;
     }
     if (bc == ORC_SC_AXIS) return field == 0 ? -own : own;
@@ -488,7 +544,9 @@ static double uy_x_neighbour(const orc_state *s, int i, int j, int di)
     if (ii >= 0 && ii < p->nz) return Uy[NODE(s, ii, j)];
     const int side = ii < 0 ? 0 : 1;
     if (p->side[side].flow == ORC_FLOW_PERIODIC) return Uy[NODE(s, (ii + p->nz) % p->nz, j)];
-    return 2.0 * p->side[side].u_wy - Uy[NODE(s, i, j)];
+    const orc_side *sd = end_side(p, side, j);
+    if (sd->flow == ORC_FLOW_FREE) return Uy[NODE(s, i, j)]; /* no shear: u_y even across the surface */
+    return 2.0 * sd->u_wy - Uy[NODE(s, i, j)];
 }
 
 static void pass2(orc_state *s, int write)
@@ -662,13 +720,16 @@ int orc_diag_compute(const orc_state *s, orc_diag *out)
     const double H = nz, Ri = p->r0, Ro = p->r0 + nr;
     double tmin = 0, tmax = 0;
     int ndir = 0;
-    for (int sd = 0; sd < 4; ++sd)
-        if (p->side[sd].heat == ORC_SC_DIRICHLET) {
-            const double t = p->side[sd].T_w;
+    for (int sd = 0; sd < 5; ++sd) {
+        const orc_side *q = sd < 4 ? &p->side[sd] : &p->top_outer;
+        if (sd == 4 && p->top_split == 0) continue;
+        if (q->heat == ORC_SC_DIRICHLET || q->heat == ORC_SC_RAMP) {
+            const double t = q->T_w;
             if (ndir == 0 || t < tmin) tmin = t;
             if (ndir == 0 || t > tmax) tmax = t;
             ++ndir;
         }
+    }
     const double dT = (ndir >= 2 && tmax > tmin) ? tmax - tmin : 1.0;
 #define TT(i, j) Tf[NODE(s, i, j)]
     if (p->side[2].heat == ORC_SC_DIRICHLET) {
@@ -710,12 +771,19 @@ int orc_diag_compute(const orc_state *s, orc_diag *out)
             sum += (p->r0 + j + 0.5) * (-8.0 * Tw + 9.0 * TT(0, j) - TT(1, j)) / 3.0;
         out->nu_side[0] = -(H / dT) * sum / area;
     }
-    if (p->side[1].heat == ORC_SC_DIRICHLET) {
-        const double Tw = p->side[1].T_w;
+    /* top: the columns whose segment holds a wall temperature (Dirichlet or
+     * the ramp), each with its own wall value */
+    {
         double sum = 0;
-        for (int j = 0; j < nr; ++j)
+        int any = 0;
+        for (int j = 0; j < nr; ++j) {
+            const int ht = end_side(p, 1, j)->heat;
+            if (ht != ORC_SC_DIRICHLET && ht != ORC_SC_RAMP) continue;
+            const double Tw = end_T(p, 1, j);
             sum += (p->r0 + j + 0.5) * (8.0 * Tw - 9.0 * TT(nz - 1, j) + TT(nz - 2, j)) / 3.0;
-        out->nu_side[1] = -(H / dT) * sum / area;
+            any = 1;
+        }
+        if (any) out->nu_side[1] = -(H / dT) * sum / area;
     }
 #undef TT
     int a = -1, b = -1;

@@ -46,8 +46,13 @@ extern "C" {
 
 /* side index: 0 = bottom (x = 0), 1 = top (x = nz), 2 = inner (y = r0),
  * 3 = outer (y = r0 + nr) */
-enum { ORC_FLOW_WALL = 0, ORC_FLOW_AXIS = 1, ORC_FLOW_PERIODIC = 2 };
-enum { ORC_SC_DIRICHLET = 0, ORC_SC_NEUMANN = 1, ORC_SC_AXIS = 2, ORC_SC_PERIODIC = 3 };
+/* ORC_FLOW_FREE: a free surface on an end wall (Sec. 3.6): zero normal
+ * velocity and zero shear, by specular reflection of f in the wall normal.
+ * ORC_SC_RAMP: a Dirichlet temperature linear in r on the outer segment of
+ * the top (Sec. 3.6): from the inner segment's T_w at the split radius to
+ * the outer segment's T_w at r0 + nr. */
+enum { ORC_FLOW_WALL = 0, ORC_FLOW_AXIS = 1, ORC_FLOW_PERIODIC = 2, ORC_FLOW_FREE = 3 };
+enum { ORC_SC_DIRICHLET = 0, ORC_SC_NEUMANN = 1, ORC_SC_AXIS = 2, ORC_SC_PERIODIC = 3, ORC_SC_RAMP = 4 };
 
 typedef struct {
     int32_t flow;    /* ORC_FLOW_*                                            */
@@ -76,6 +81,11 @@ typedef struct {
     int32_t explicit_sources; /* 1: sources at the output state only      */
     int32_t pad;
     orc_side side[4];
+    /* the top may consist of two segments (Sec. 3.6, a crystal inside a free
+     * surface): columns j >= top_split follow top_outer; 0 = one segment */
+    int32_t top_split;
+    int32_t pad2;
+    orc_side top_outer;
 } orc_params;
 
 typedef struct {

@@ -19,8 +19,8 @@ import numpy as np
 
 # side indices and boundary codes shared by the C ABI (include/lb.h)
 BOTTOM, TOP, INNER, OUTER = 0, 1, 2, 3
-FLOW_WALL, FLOW_AXIS, FLOW_PERIODIC = 0, 1, 2
-SC_DIRICHLET, SC_NEUMANN, SC_AXIS, SC_PERIODIC = 0, 1, 2, 3
+FLOW_WALL, FLOW_AXIS, FLOW_PERIODIC, FLOW_FREE = 0, 1, 2, 3
+SC_DIRICHLET, SC_NEUMANN, SC_AXIS, SC_PERIODIC, SC_RAMP = 0, 1, 2, 3, 4
 
 CS = 1.0 / math.sqrt(3.0)  # lattice speed of sound
 
