@@ -187,7 +187,7 @@ def oracle_mlups(nr, nz_full, budget_s, max_rows=None):
                       f"{dt:.1f} s"}
 
 
-def serving_measure(requests, nr_lo, nr_hi, max_steps, storage):
+def serving_measure(requests, nr_lo, nr_hi, max_steps, storage, node_budget=0):
     """A Poisson stream of solve requests (rate 50/s, seed 0) served by the
     continuous-batching server (autotuned batched launches, graphs of 10) and,
     for comparison, by sequential plain FP32 solves; both with the steady
@@ -197,7 +197,7 @@ def serving_measure(requests, nr_lo, nr_hi, max_steps, storage):
     from paper_1806_10241_gb300.serving import Server
     reqs = W.serving_requests(count=requests, rate=50.0, seed=0, nr_lo=nr_lo, nr_hi=nr_hi)
     kw = dict(steps_per_round=500, check_every=500, window=1000, tol=1e-6, max_steps=max_steps)
-    srv = Server(storage=storage, graph_steps=10, autotune=True, **kw)
+    srv = Server(storage=storage, graph_steps=10, autotune=True, node_budget=node_budget or None, **kw)
     rep_b = srv.run(reqs)
     rep_s = Server(storage=storage, **kw).run_sequential(reqs, storage="fp32")
     torch.cuda.synchronize()
@@ -211,7 +211,9 @@ def serving_measure(requests, nr_lo, nr_hi, max_steps, storage):
             "config": {"requests": requests, "rate_per_s": 50.0, "nr": f"U{{{nr_lo}..{nr_hi}}}",
                        "nz": "nr * U{1,2}", "Ra": "log-U[1e3,1e5]", "mix": "60 % annulus, 40 % cylinder",
                        "steady": "|dNu| < 1e-6 over 1000 steps", "max_steps": max_steps, "storage": storage,
-                       "batch_launch": "autotuned per size class"},
+                       "batch_launch": "autotuned per size class",
+                       "admission": "free HBM" + (f" and at most {node_budget} nodes stepped together"
+                                                  if node_budget else "")},
             "nu_rel_diff_vs_sequential_fp32": {"max": float(max(dnu)) if dnu else None,
                                                "median": float(sorted(dnu)[len(dnu) // 2]) if dnu else None},
             "batched": rb, "sequential_fp32": seq,
@@ -230,7 +232,8 @@ def run_serving(args):
     import __graft_entry__
     __graft_entry__.build()
     torch.cuda.set_device(0)
-    m = serving_measure(args.requests, args.nr_lo, args.nr_hi, args.max_steps, args.serve_storage)
+    m = serving_measure(args.requests, args.nr_lo, args.nr_hi, args.max_steps, args.serve_storage,
+                        args.serve_node_budget)
     line = {"metric": METRIC, "value": m["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.serve_storage], "data": "synthetic",
@@ -530,6 +533,8 @@ def main():
     ap.add_argument("--repeats", type=int, default=0,
                     help="timed regions of K steps (0: automatic, 5..20); the line reports the median")
     ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=16)
+    ap.add_argument("--serve-node-budget", dest="serve_node_budget", type=int, default=0,
+                    help="--workload serving: at most this many nodes stepped together (0: HBM admission only)")
     ap.add_argument("--serve-max-steps", dest="serve_max_steps", type=int, default=50_000)
     ap.add_argument("--workload", default="cylinder", choices=["cylinder", "serving", "precision", "batch"])
     ap.add_argument("--instances", type=int, default=256)

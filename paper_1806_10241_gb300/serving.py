@@ -5,7 +5,11 @@ server keeps every admitted lattice resident on the device and advances all
 of them together with the batched step (one persistent launch per step,
 replayed from a CUDA graph).  Between rounds it
   * admits the requests that have arrived while their bytes fit the device
-    memory budget (lb_required_bytes against free HBM less a reserve),
+    memory budget (lb_required_bytes against free HBM less a reserve) and,
+    when node_budget is set, while the nodes being stepped stay within it
+    (a lone request is always admitted): once the resident lattices fill
+    the GPU, more of them only lengthen every active request's latency
+    without raising the update rate, so the rest wait in arrival order,
   * evaluates the diagnostics of each active lattice every `check_every`
     steps and retires the ones that reached the steady state
     (|Nu(t) - Nu(t - window)| < tol), hit the step cap or diverged,
@@ -96,7 +100,8 @@ class Server:
                  window: int = 1000, tol: float = 1e-6, max_steps: int = 200_000,
                  hbm_budget: int | None = None, reserve_bytes: int = 1 << 30, max_active: int = 512,
                  graph_steps: int = 10, seg_rows: int = 0, warps_per_block: int = 0,
-                 device: str = "cuda", keep_results: bool = False, autotune: bool = False):
+                 device: str = "cuda", keep_results: bool = False, autotune: bool = False,
+                 node_budget: int | None = None):
         if check_every % steps_per_round:
             raise ValueError("check_every must be a multiple of steps_per_round")
         self.storage = storage
@@ -106,6 +111,8 @@ class Server:
         self.tol = tol
         self.max_steps = max_steps
         self.max_active = max_active
+        self.node_budget = node_budget
+        self.max_nodes = 0  # most nodes stepped together
         self.graph_steps = graph_steps
         self.seg_rows = seg_rows
         self.warps_per_block = warps_per_block
@@ -156,6 +163,7 @@ class Server:
         records = {r.rid: Record(r.rid, r.case.name, r.case.nr * r.case.nz, r.arrival) for r in requests}
         active: list[_Active] = []
         used = 0
+        nodes = 0
         batch = None
         dirty = True
         t0 = clock()
@@ -182,10 +190,15 @@ class Server:
                     continue
                 if used + need > self.budget:
                     break
+                n_req = pending[0].case.nr * pending[0].case.nz
+                if self.node_budget and active and nodes + n_req > self.node_budget:
+                    break
                 req = pending.popleft()
                 active.append(self._admit(req, now, records[req.rid]))
                 used += active[-1].nbytes
+                nodes += n_req
                 self.max_concurrent = max(self.max_concurrent, len(active))
+                self.max_nodes = max(self.max_nodes, nodes)
                 dirty = True
             if not active:
                 if pending:
@@ -221,6 +234,7 @@ class Server:
                     if self.keep_results:
                         self.results[a.rec.rid] = a.solver.get_dist()
                     used -= a.nbytes
+                    nodes -= a.rec.nodes
                     active.remove(a)
                     a.solver.close()
                 batch.close()
@@ -230,7 +244,8 @@ class Server:
             batch.close()
         torch.cuda.synchronize(self.device)
         return Report(list(records.values()), clock() - t0, "batched",
-                      {"rounds": rounds, "storage": self.storage, "max_concurrent": self.max_concurrent})
+                      {"rounds": rounds, "storage": self.storage, "max_concurrent": self.max_concurrent,
+                       "max_nodes": self.max_nodes, "node_budget": self.node_budget})
 
     def run_sequential(self, requests: list[Request], storage: str = "fp32",
                        clock=time.perf_counter) -> Report:

@@ -151,3 +151,22 @@ def test_autotuned_server_gives_the_same_results_as_solo_runs():
         s.init_fields(req.case.fields)
         s.step(r.steps)
         assert np.array_equal(srv.results[r.rid], s.get_dist()), r.rid
+
+
+def test_node_budget_limits_the_lattices_stepped_together():
+    """With a node budget the server steps at most that many nodes at once
+    (a lone larger request excepted), queues the rest in arrival order, and
+    every request still finishes with the result of a solo run."""
+    from paper_1806_10241_gb300.serving import Server
+    reqs = [W.Request(r.rid, 0.0, r.case) for r in _stream()]  # all waiting at the start
+    budget = 2 * max(r.case.nr * r.case.nz for r in reqs)
+    srv = Server(storage="fp32", steps_per_round=100, check_every=200, window=400, tol=1e-7,
+                 max_steps=1000, keep_results=True, graph_steps=5, node_budget=budget)
+    rep = srv.run(reqs)
+    assert rep.summary()["completed"] == len(reqs)
+    assert 2 <= srv.max_concurrent < len(reqs)
+    assert srv.max_nodes <= budget
+    admitted = sorted(rep.records, key=lambda r: (r.admitted, r.rid))
+    assert [r.rid for r in admitted] == sorted(r.rid for r in rep.records)  # arrival order
+    for r in rep.records:
+        assert np.array_equal(srv.results[r.rid], _alone(reqs[r.rid], r.steps, "fp32", 100)), r.name
