@@ -83,16 +83,27 @@ enum { LB_SIDE_BOTTOM = 0, LB_SIDE_TOP = 1, LB_SIDE_INNER = 2, LB_SIDE_OUTER = 3
  *   sliding wall, a normal u_w a porous wall.
  * LB_FLOW_AXIS: the symmetry line r = 0, mirror rule for the particle
  *   distributions (Sec. 3.3); only on the inner side with r_inner = 0.
- * LB_FLOW_PERIODIC: periodic along z (Sec. 3.1); bottom and top together. */
-enum { LB_FLOW_WALL = 0, LB_FLOW_AXIS = 1, LB_FLOW_PERIODIC = 2 };
+ * LB_FLOW_PERIODIC: periodic along z (Sec. 3.1); bottom and top together.
+ * LB_FLOW_FREE: a free surface on an end wall (Sec. 3.6: u_z = 0,
+ *   d u_r / dz = 0): specular reflection of the particle distributions in
+ *   the wall normal, and an even u_r across it for the central differences.
+ *   Where the reflected source lies beyond a lateral side (a corner), the
+ *   side's own rule applies to the node itself: across the axis the mirror
+ *   image, at a wall the bounce-back with that wall's momentum term. */
+enum { LB_FLOW_WALL = 0, LB_FLOW_AXIS = 1, LB_FLOW_PERIODIC = 2, LB_FLOW_FREE = 3 };
 
 /* Scalar (g: psi, h: T) boundary types.
  * LB_SC_DIRICHLET: anti-bounce-back to a wall value (Sec. 3.1, 3.2): for g
  *   psi_w = rho0 * omega * radius (a rotating wall: the column's radius on an
  *   end wall, the wall radius on a lateral wall), for h the value T_w.
  * LB_SC_NEUMANN: zero flux (bounce-back), e.g. an adiabatic wall.
- * LB_SC_AXIS: symmetry line (psi odd, T even).  LB_SC_PERIODIC: along z. */
-enum { LB_SC_DIRICHLET = 0, LB_SC_NEUMANN = 1, LB_SC_AXIS = 2, LB_SC_PERIODIC = 3 };
+ * LB_SC_AXIS: symmetry line (psi odd, T even).  LB_SC_PERIODIC: along z.
+ * LB_SC_RAMP: for h on the outer segment of a split top only (Sec. 3.6, the
+ *   melt surface beyond the crystal): Dirichlet to a wall temperature
+ *   linear in r, from the inner segment's T_w at the split radius
+ *   r_inner + top_split to the outer segment's T_w at r_inner + nr, taken at
+ *   each column's radius. */
+enum { LB_SC_DIRICHLET = 0, LB_SC_NEUMANN = 1, LB_SC_AXIS = 2, LB_SC_PERIODIC = 3, LB_SC_RAMP = 4 };
 
 typedef struct {
     int32_t flow;    /* LB_FLOW_*                                          */
@@ -114,7 +125,12 @@ typedef struct {
  *   explicit_sources = 1 evaluates the sources once at the post-streaming
  *   state (the literal reading; see the readings of the paper).  The default
  *   evaluates them at the pre-collision state by two local sweeps.
- *   sign_literal = 1 uses the sign printed in Eq. 34 / 49. */
+ *   sign_literal = 1 uses the sign printed in Eq. 34 / 49.
+ *   top_split > 0 splits the top into two segments (Sec. 3.6: the crystal
+ *   and the free melt surface around it): columns j < top_split follow
+ *   side[LB_SIDE_TOP], columns j >= top_split follow top_outer (flow WALL or
+ *   FREE; swirl DIRICHLET or NEUMANN; heat DIRICHLET, NEUMANN or RAMP).
+ *   0 <= top_split < nr; 0 = one segment (top_outer unused). */
 typedef struct {
     double nu, alpha, omega3, omega_hi, g_beta, T0, body_fx, rho0;
     int32_t planar;
@@ -122,6 +138,9 @@ typedef struct {
     int32_t explicit_sources;
     int32_t pad;
     lb_side side[4];
+    int32_t top_split;
+    int32_t pad2;
+    lb_side top_outer;
 } lb_params;
 
 /* Diagnostics (Sec. 3.2): Nusselt number on each Dirichlet-T side
@@ -135,7 +154,9 @@ typedef struct {
  * of an annulus) -- all accumulated in FP64 from the pre-collision fields of
  * the current state.  Wall derivatives are one-sided and second order
  * through the wall value, (-8 T_w + 9 T_1 - T_2) / 3 along the inward
- * normal; sums over the wall are midpoint sums. */
+ * normal; sums over the wall are midpoint sums.  On a split top the sum
+ * covers the columns whose segment holds a wall temperature (DIRICHLET or
+ * RAMP), each with its own wall value. */
 typedef struct {
     double nu_side[4];
     double nu_i, nu_o, nu_avg;

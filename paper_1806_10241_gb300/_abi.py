@@ -36,7 +36,8 @@ class lb_params(C.Structure):
                 ("omega_hi", C.c_double), ("g_beta", C.c_double), ("T0", C.c_double),
                 ("body_fx", C.c_double), ("rho0", C.c_double), ("planar", C.c_int32),
                 ("sign_literal", C.c_int32), ("explicit_sources", C.c_int32),
-                ("pad", C.c_int32), ("side", lb_side * 4)]
+                ("pad", C.c_int32), ("side", lb_side * 4), ("top_split", C.c_int32), ("pad2", C.c_int32),
+                ("top_outer", lb_side)]
 
 
 class lb_diag(C.Structure):
@@ -131,14 +132,19 @@ def make_params(d: dict) -> lb_params:
     p.planar = int(d.get("planar", 0))
     p.sign_literal = int(d.get("sign_literal", 0))
     p.explicit_sources = int(d.get("explicit_sources", 0))
+    def fill(dst, s):
+        dst.flow = int(s.get("flow", 0))
+        dst.swirl = int(s.get("swirl", 0))
+        dst.heat = int(s.get("heat", 1))
+        dst.u_wx = float(s.get("u_wx", 0.0))
+        dst.u_wy = float(s.get("u_wy", 0.0))
+        dst.omega = float(s.get("omega", 0.0))
+        dst.T_w = float(s.get("T_w", 0.0))
     for i, s in enumerate(d["sides"]):
-        p.side[i].flow = int(s.get("flow", 0))
-        p.side[i].swirl = int(s.get("swirl", 0))
-        p.side[i].heat = int(s.get("heat", 1))
-        p.side[i].u_wx = float(s.get("u_wx", 0.0))
-        p.side[i].u_wy = float(s.get("u_wy", 0.0))
-        p.side[i].omega = float(s.get("omega", 0.0))
-        p.side[i].T_w = float(s.get("T_w", 0.0))
+        fill(p.side[i], s)
+    p.top_split = int(d.get("top_split", 0))
+    if "top_outer" in d:
+        fill(p.top_outer, d["top_outer"])
     return p
 
 

@@ -131,7 +131,7 @@ lb_status lbk::host_set_params(const lb_params *p, HostParams *h, char *err, siz
     if (per0 != per1) return say(err, n, LB_ERR_ARG, "periodicity needs both end sides");
     for (int s = 0; s < 4; ++s) {
         const lb_side &sd = p->side[s];
-        if (sd.flow < 0 || sd.flow > 2 || sd.swirl < 0 || sd.swirl > 3 || sd.heat < 0 || sd.heat > 3)
+        if (sd.flow < 0 || sd.flow > 3 || sd.swirl < 0 || sd.swirl > 4 || sd.heat < 0 || sd.heat > 4)
             return say(err, n, LB_ERR_ARG, "side %d: unknown boundary code", s);
         const bool per = sd.flow == LB_FLOW_PERIODIC;
         const bool ax = sd.flow == LB_FLOW_AXIS;
@@ -148,6 +148,25 @@ lb_status lbk::host_set_params(const lb_params *p, HostParams *h, char *err, siz
     }
     if (h->r0 == 0.0 && !p->planar && p->side[2].flow != LB_FLOW_AXIS)
         return say(err, n, LB_ERR_ARG, "r_inner = 0 needs the axis on the inner side");
+    for (int s = 0; s < 4; ++s) {
+        const lb_side &sd = p->side[s];
+        if (sd.flow == LB_FLOW_FREE && s >= 2) return say(err, n, LB_ERR_ARG, "a free surface only on an end wall");
+        if (sd.heat == LB_SC_RAMP || sd.swirl == LB_SC_RAMP)
+            return say(err, n, LB_ERR_ARG, "the temperature ramp only on the outer segment of a split top");
+    }
+    if (p->top_split < 0 || p->top_split >= h->nr) return say(err, n, LB_ERR_ARG, "top_split must lie in 0..nr-1");
+    if (p->top_split > 0) {
+        const lb_side &t = p->top_outer;
+        if (p->side[1].flow == LB_FLOW_PERIODIC) return say(err, n, LB_ERR_ARG, "a periodic top cannot be split");
+        if (!(t.flow == LB_FLOW_WALL || t.flow == LB_FLOW_FREE) ||
+            !(t.swirl == LB_SC_DIRICHLET || t.swirl == LB_SC_NEUMANN) ||
+            !(t.heat == LB_SC_DIRICHLET || t.heat == LB_SC_NEUMANN || t.heat == LB_SC_RAMP))
+            return say(err, n, LB_ERR_ARG, "top_outer: flow WALL or FREE, swirl DIRICHLET or NEUMANN, "
+                                           "heat DIRICHLET, NEUMANN or RAMP");
+        const double tv[4] = {t.u_wx, t.u_wy, t.omega, t.T_w};
+        for (double v : tv)
+            if (!std::isfinite(v)) return say(err, n, LB_ERR_ARG, "top_outer: non-finite wall value");
+    }
     h->nu = p->nu;
     h->alpha = p->alpha;
     h->omega3 = p->omega3;
@@ -159,15 +178,18 @@ lb_status lbk::host_set_params(const lb_params *p, HostParams *h, char *err, siz
     h->planar = p->planar;
     h->sign_literal = p->sign_literal;
     h->explicit_sources = p->explicit_sources;
-    for (int s = 0; s < 4; ++s) {
-        h->flow[s] = p->side[s].flow;
-        h->swirl[s] = p->side[s].swirl;
-        h->heat[s] = p->side[s].heat;
-        h->uwx[s] = p->side[s].u_wx;
-        h->uwy[s] = p->side[s].u_wy;
-        h->omega[s] = p->side[s].omega;
-        h->Tw[s] = p->side[s].T_w;
+    for (int s = 0; s < 5; ++s) {
+        // entry 4: the top's outer segment, or a copy of the top when it is not split
+        const lb_side &sd = s < 4 ? p->side[s] : (p->top_split > 0 ? p->top_outer : p->side[1]);
+        h->flow[s] = sd.flow;
+        h->swirl[s] = sd.swirl;
+        h->heat[s] = sd.heat;
+        h->uwx[s] = sd.u_wx;
+        h->uwy[s] = sd.u_wy;
+        h->omega[s] = sd.omega;
+        h->Tw[s] = sd.T_w;
     }
+    h->top_split = p->top_split;
     return LB_OK;
 }
 

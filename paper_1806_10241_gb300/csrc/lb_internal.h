@@ -29,8 +29,10 @@ struct HostParams {
     double r0;
     double nu, alpha, omega3, omega_hi, g_beta, T0, body_fx, rho0;
     int planar, sign_literal, explicit_sources;
-    int flow[4], swirl[4], heat[4];
-    double uwx[4], uwy[4], omega[4], Tw[4];
+    // sides 0..3 as lb_side; entry 4 the outer segment of a split top
+    int flow[5], swirl[5], heat[5];
+    double uwx[5], uwy[5], omega[5], Tw[5];
+    int top_split;            // columns >= top_split of the top follow entry 4 (0: one segment)
     double scale;             // storage scale of the deviations (16-bit)
     const float *ytab;        // device table: y[pitch] then 1/y[pitch] (FP64, rounded once)
 };

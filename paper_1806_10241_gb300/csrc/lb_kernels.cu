@@ -87,8 +87,12 @@ template <typename C> struct KP {
     C om3, om4, omhi, omg, omh;
     C nu, alpha, gbeta, T0, bfx, rho0;
     int planar, sign_lit, explicit_src;
-    int flow[4], swirl[4], heat[4];
-    C uwx[4], uwy[4], omega[4], Tw[4];
+    // sides 0..3; entry 4 the outer segment of a split top (a copy of the top
+    // when the top is one segment): columns >= top_split of the top follow it
+    int flow[5], swirl[5], heat[5];
+    C uwx[5], uwy[5], omega[5], Tw[5];
+    int top_split;
+    C ramp0, ramp1;       // wall temperature ramp of entry 4: T_w(y) = ramp0 + ramp1 y
     C scale, inv_scale;
     C r0c, roc;           // inner and outer wall radii, rounded once
     const float *ytab;    // y[pitch] then 1/y[pitch] (pair kernels)
@@ -120,7 +124,7 @@ template <typename C> KP<C> make_kp(const HostParams &h)
     k.planar = h.planar;
     k.sign_lit = h.sign_literal;
     k.explicit_src = h.explicit_sources;
-    for (int s = 0; s < 4; ++s) {
+    for (int s = 0; s < 5; ++s) {
         k.flow[s] = h.flow[s];
         k.swirl[s] = h.swirl[s];
         k.heat[s] = h.heat[s];
@@ -128,6 +132,14 @@ template <typename C> KP<C> make_kp(const HostParams &h)
         k.uwy[s] = (C)h.uwy[s];
         k.omega[s] = (C)h.omega[s];
         k.Tw[s] = (C)h.Tw[s];
+    }
+    k.top_split = h.top_split;
+    {  // Sec. 3.6 surface temperature: linear in r from the top's T_w at the
+       // split radius to the outer segment's T_w at the outer wall
+        const double rs = h.r0 + h.top_split, ro = h.r0 + h.nr;
+        const double slope = h.top_split > 0 ? (h.Tw[4] - h.Tw[1]) / (ro - rs) : 0.0;
+        k.ramp0 = (C)(h.Tw[1] - slope * rs);
+        k.ramp1 = (C)slope;
     }
     k.scale = (C)h.scale;
     k.inv_scale = (C)(1.0 / h.scale);
@@ -138,8 +150,8 @@ template <typename C> KP<C> make_kp(const HostParams &h)
     // walls -(H / dT) * 2 / (R_o^2 - R_i^2); dT from the Dirichlet values.
     double tmin = 0, tmax = 0;
     int nd = 0;
-    for (int s = 0; s < 4; ++s)
-        if (h.heat[s] == 0) {
+    for (int s = 0; s < 5; ++s)
+        if ((h.heat[s] == 0 || h.heat[s] == 4) && (s < 4 || h.top_split > 0)) {
             if (nd == 0 || h.Tw[s] < tmin) tmin = h.Tw[s];
             if (nd == 0 || h.Tw[s] > tmax) tmax = h.Tw[s];
             ++nd;
@@ -248,11 +260,37 @@ __device__ __forceinline__ C own(const S *__restrict__ src, const KP<C> &k, int 
     return Cvt<S, C>::ld(src + q * k.plane + (long long)row * k.pitch + col);
 }
 
-// psi on a rotating wall: rho0 * omega * radius
+// psi on a rotating wall: rho0 * omega * radius (side 4: the top's outer segment)
 template <typename C> __device__ __forceinline__ C wall_psi(const KP<C> &k, int side, C y)
 {
-    const C radius = side <= 1 ? y : (side == 2 ? k.r0c : k.roc);
+    const C radius = (side <= 1 || side == 4) ? y : (side == 2 ? k.r0c : k.roc);
     return k.rho0 * k.omega[side] * radius;
+}
+
+// the entry of an end wall at column col: the top's outer segment (4) for
+// columns >= top_split of a split top, else the side itself
+template <typename C> __device__ __forceinline__ int end_seg(const KP<C> &k, int side, int col)
+{
+    return (side == 1 && k.top_split > 0 && col >= k.top_split) ? 4 : side;
+}
+
+// wall temperature of an end-wall entry at the column radius y (the ramp of
+// Sec. 3.6 on entry 4 with heat type 4), and the entry's h rule with the ramp
+// read as Dirichlet
+template <typename C> __device__ __forceinline__ C end_T(const KP<C> &k, int seg, C y)
+{
+    return k.heat[seg] == 4 ? k.ramp0 + k.ramp1 * y : k.Tw[seg];
+}
+template <typename C> __device__ __forceinline__ int heat_rule(const KP<C> &k, int seg)
+{
+    return k.heat[seg] == 4 ? 0 : k.heat[seg];
+}
+// a side whose wall temperatures enter its Nusselt number (Sec. 3.2): a
+// Dirichlet side, or a top any of whose segments holds a wall temperature
+template <typename C> __device__ __forceinline__ bool wall_heated(const KP<C> &k, int sd)
+{
+    if (sd == 1 && k.top_split > 0) return k.heat[1] == 0 || k.heat[4] == 0 || k.heat[4] == 4;
+    return k.heat[sd] == 0;
 }
 
 // Scalar boundary value for the population entering from a wall (Sec. 3):
@@ -521,24 +559,47 @@ __device__ __forceinline__ void march(const KP<C> &k, const S *__restrict__ src,
                 hv[4] = scalar_bc<C>(k.heat[sd], own<S, C>(src, k, H0 + 2, i, nr - 1), (k.Tw[sd] - k.T0) * sc, false);
             }
         }
-        // end walls (rows 0 and nz-1 unless periodic); they win in corners
+        // end walls (rows 0 and nz-1 unless periodic); they win in corners.  A
+        // free surface (Sec. 3.6) reflects f specularly: the population that
+        // left the neighbour column towards the wall, e_x reversed; at a corner
+        // column the lateral side's rule for the node itself
         if (!has_m) {
-            const int sd = 0;
+            const int sd = end_seg(k, 0, cl);
             const C rw = k.rho0 * sc, ux_w = k.uwx[sd], uy_w = k.uwy[sd];
-            fv[1] = own<S, C>(src, k, 3, i, cl) + rw * (C)(6.0 / 9.0) * ux_w;
-            fv[5] = own<S, C>(src, k, 7, i, cl) + rw * (C)(6.0 / 36.0) * (ux_w + uy_w);
-            fv[8] = own<S, C>(src, k, 6, i, cl) + rw * (C)(6.0 / 36.0) * (ux_w - uy_w);
+            if (k.flow[sd] == 3) {
+                fv[1] = own<S, C>(src, k, 3, i, cl);
+                fv[5] = at_c0 ? own<S, C>(src, k, 7, i, 0) +
+                                    (k.flow[2] == 1 ? (C)0 : rw * (C)(6.0 / 36.0) * (k.uwx[2] + k.uwy[2]))
+                              : own<S, C>(src, k, 6, i, cl > 0 ? cl - 1 : 0);
+                fv[8] = at_cN ? own<S, C>(src, k, 6, i, cl) + rw * (C)(6.0 / 36.0) * (k.uwx[3] - k.uwy[3])
+                              : own<S, C>(src, k, 7, i, cl + 1 < nr ? cl + 1 : cl);
+            } else {
+                fv[1] = own<S, C>(src, k, 3, i, cl) + rw * (C)(6.0 / 9.0) * ux_w;
+                fv[5] = own<S, C>(src, k, 7, i, cl) + rw * (C)(6.0 / 36.0) * (ux_w + uy_w);
+                fv[8] = own<S, C>(src, k, 6, i, cl) + rw * (C)(6.0 / 36.0) * (ux_w - uy_w);
+            }
             gv[1] = scalar_bc<C>(k.swirl[sd], own<S, C>(src, k, G0 + 3, i, cl), wall_psi<C>(k, sd, y) * sc, true);
-            hv[1] = scalar_bc<C>(k.heat[sd], own<S, C>(src, k, H0 + 3, i, cl), (k.Tw[sd] - k.T0) * sc, false);
+            hv[1] = scalar_bc<C>(heat_rule(k, sd), own<S, C>(src, k, H0 + 3, i, cl), (end_T(k, sd, y) - k.T0) * sc,
+                                 false);
         }
         if (!has_p) {
-            const int sd = 1;
+            const int sd = end_seg(k, 1, cl);
             const C rw = k.rho0 * sc, ux_w = k.uwx[sd], uy_w = k.uwy[sd];
-            fv[3] = own<S, C>(src, k, 1, i, cl) + rw * (C)(6.0 / 9.0) * (-ux_w);
-            fv[6] = own<S, C>(src, k, 8, i, cl) + rw * (C)(6.0 / 36.0) * (-ux_w + uy_w);
-            fv[7] = own<S, C>(src, k, 5, i, cl) + rw * (C)(6.0 / 36.0) * (-ux_w - uy_w);
+            if (k.flow[sd] == 3) {
+                fv[3] = own<S, C>(src, k, 1, i, cl);
+                fv[6] = at_c0 ? own<S, C>(src, k, 8, i, 0) +
+                                    (k.flow[2] == 1 ? (C)0 : rw * (C)(6.0 / 36.0) * (-k.uwx[2] + k.uwy[2]))
+                              : own<S, C>(src, k, 5, i, cl > 0 ? cl - 1 : 0);
+                fv[7] = at_cN ? own<S, C>(src, k, 5, i, cl) + rw * (C)(6.0 / 36.0) * (-k.uwx[3] - k.uwy[3])
+                              : own<S, C>(src, k, 8, i, cl + 1 < nr ? cl + 1 : cl);
+            } else {
+                fv[3] = own<S, C>(src, k, 1, i, cl) + rw * (C)(6.0 / 9.0) * (-ux_w);
+                fv[6] = own<S, C>(src, k, 8, i, cl) + rw * (C)(6.0 / 36.0) * (-ux_w + uy_w);
+                fv[7] = own<S, C>(src, k, 5, i, cl) + rw * (C)(6.0 / 36.0) * (-ux_w - uy_w);
+            }
             gv[3] = scalar_bc<C>(k.swirl[sd], own<S, C>(src, k, G0 + 1, i, cl), wall_psi<C>(k, sd, y) * sc, true);
-            hv[3] = scalar_bc<C>(k.heat[sd], own<S, C>(src, k, H0 + 1, i, cl), (k.Tw[sd] - k.T0) * sc, false);
+            hv[3] = scalar_bc<C>(heat_rule(k, sd), own<S, C>(src, k, H0 + 1, i, cl), (end_T(k, sd, y) - k.T0) * sc,
+                                 false);
         }
         if (Scaled<S>::value) {
 #pragma unroll
@@ -551,8 +612,10 @@ __device__ __forceinline__ void march(const KP<C> &k, const S *__restrict__ src,
         }
 
         // central differences of the stored-state fields, with ghosts
-        const C uy_xm = has_m ? uy_prev : (C)2 * k.uwy[0] - pm_cur.uy;
-        const C uy_xp = has_p ? pm_n.uy : (C)2 * k.uwy[1] - pm_cur.uy;
+        // (a free surface: no shear, u_y even across it)
+        const int sb = end_seg(k, 0, cl), st = end_seg(k, 1, cl);
+        const C uy_xm = has_m ? uy_prev : (k.flow[sb] == 3 ? pm_cur.uy : (C)2 * k.uwy[sb] - pm_cur.uy);
+        const C uy_xp = has_p ? pm_n.uy : (k.flow[st] == 3 ? pm_cur.uy : (C)2 * k.uwy[st] - pm_cur.uy);
         C ux_l = shup(pm_cur.ux), uy_l = shup(pm_cur.uy), ut_l = shup(pm_cur.ut), T_l = shup(pm_cur.T);
         C ux_r = shdn(pm_cur.ux), uy_r = shdn(pm_cur.uy), ut_r = shdn(pm_cur.ut), T_r = shdn(pm_cur.T);
         if (edge_warp) {
@@ -921,7 +984,7 @@ __device__ __forceinline__ void wall_block(const KP<C> &k, const double *__restr
     const int nr = k.nr, nz = k.nz;
     for (int sd = 0; sd < 4; ++sd) {
         double acc = 0;
-        if (k.heat[sd] == 0) {
+        if (wall_heated(k, sd)) {
             const double Tw = (double)k.Tw[sd];
             if (sd == 2)
                 for (int i = threadIdx.x; i < nz; i += blockDim.x)
@@ -932,10 +995,14 @@ __device__ __forceinline__ void wall_block(const KP<C> &k, const double *__restr
             else if (sd == 0)
                 for (int j = threadIdx.x; j < nr; j += blockDim.x)
                     acc += (k.r0 + j + 0.5) * (-8.0 * Tw + 9.0 * T[j] - T[nr + j]) / 3.0;
-            else
-                for (int j = threadIdx.x; j < nr; j += blockDim.x)
+            else  // the top: the columns whose segment holds a wall temperature, each with its own value
+                for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+                    const int sg = end_seg(k, 1, j);
+                    if (k.heat[sg] != 0 && k.heat[sg] != 4) continue;
+                    const double Tj = (double)end_T(k, sg, (C)(k.r0 + j + 0.5));
                     acc += (k.r0 + j + 0.5) *
-                           (8.0 * Tw - 9.0 * T[(long long)(nz - 1) * nr + j] + T[(long long)(nz - 2) * nr + j]) / 3.0;
+                           (8.0 * Tj - 9.0 * T[(long long)(nz - 1) * nr + j] + T[(long long)(nz - 2) * nr + j]) / 3.0;
+                }
         }
         sh[threadIdx.x] = acc;
         __syncthreads();
@@ -944,7 +1011,7 @@ __device__ __forceinline__ void wall_block(const KP<C> &k, const double *__restr
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            result[4 + sd] = k.heat[sd] == 0 ? sh[0] * k.nu_scale[sd] : 0.0;
+            result[4 + sd] = wall_heated(k, sd) ? sh[0] * k.nu_scale[sd] : 0.0;
             if (sd >= 2) result[7 + sd] = k.heat[sd] == 0 ? sh[0] * k.keq_scale[sd] : 0.0;  // 9, 10: k_eq
         }
         __syncthreads();
@@ -998,7 +1065,7 @@ __global__ void __launch_bounds__(256) k_wall_strip(KP<C> k, const double *__res
     const double *c0 = strips + 4 * nr, *c1 = c0 + nz, *c2 = c0 + 2 * nz, *c3 = c0 + 3 * nz;
     for (int sd = 0; sd < 4; ++sd) {
         double acc = 0;
-        if (k.heat[sd] == 0) {
+        if (wall_heated(k, sd)) {
             const double Tw = (double)k.Tw[sd];
             if (sd == 2)
                 for (int i = threadIdx.x; i < nz; i += blockDim.x) acc += (-8.0 * Tw + 9.0 * c0[i] - c1[i]) / 3.0;
@@ -1008,8 +1075,12 @@ __global__ void __launch_bounds__(256) k_wall_strip(KP<C> k, const double *__res
                 for (int j = threadIdx.x; j < nr; j += blockDim.x)
                     acc += (k.r0 + j + 0.5) * (-8.0 * Tw + 9.0 * r0[j] - r1[j]) / 3.0;
             else
-                for (int j = threadIdx.x; j < nr; j += blockDim.x)
-                    acc += (k.r0 + j + 0.5) * (8.0 * Tw - 9.0 * r3[j] + r2[j]) / 3.0;
+                for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+                    const int sg = end_seg(k, 1, j);
+                    if (k.heat[sg] != 0 && k.heat[sg] != 4) continue;
+                    const double Tj = (double)end_T(k, sg, (C)(k.r0 + j + 0.5));
+                    acc += (k.r0 + j + 0.5) * (8.0 * Tj - 9.0 * r3[j] + r2[j]) / 3.0;
+                }
         }
         sh[threadIdx.x] = acc;
         __syncthreads();
@@ -1018,7 +1089,7 @@ __global__ void __launch_bounds__(256) k_wall_strip(KP<C> k, const double *__res
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            result[4 + sd] = k.heat[sd] == 0 ? sh[0] * k.nu_scale[sd] : 0.0;
+            result[4 + sd] = wall_heated(k, sd) ? sh[0] * k.nu_scale[sd] : 0.0;
             if (sd >= 2) result[7 + sd] = k.heat[sd] == 0 ? sh[0] * k.keq_scale[sd] : 0.0;  // 9, 10: k_eq
         }
         __syncthreads();

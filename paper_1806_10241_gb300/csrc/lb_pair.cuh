@@ -600,6 +600,10 @@ __device__ __forceinline__ void halo_fields(const KP<float> &k, const float h[NQ
 // and f7 on row i + 1 at column 0, for the axis mirror).  OwnGlobal reads them
 // from the source buffer; OwnStage from the TMA ring, where they already are,
 // so that a warp at a wall or the axis waits on no global load.
+// shl(q) / shr(q): the pair's values of plane q one column to the left
+// (A - 1, A) and to the right (A + 1, A + 2) on row i (free-surface end walls;
+// columns outside the lattice are clamped, their values replaced by the
+// corner rules).
 template <typename S> struct OwnGlobal {
     const S *src;
     const KP<float> *k;
@@ -608,6 +612,13 @@ template <typename S> struct OwnGlobal {
     __device__ __forceinline__ float own0(int q) const { return own2<S>(src, *k, q, i, 0).v.x; }
     __device__ __forceinline__ float m8() const { return own2<S>(src, *k, 8, i > 0 ? i - 1 : k->nz - 1, 0).v.x; }
     __device__ __forceinline__ float p7() const { return own2<S>(src, *k, 7, i + 1 < k->nz ? i + 1 : 0, 0).v.x; }
+    __device__ __forceinline__ float at(int q, int col) const
+    {
+        col = col < 0 ? 0 : (col >= k->nr ? k->nr - 1 : col);
+        return LoadScaled<S>::one(src + q * k->plane + (long long)i * k->pitch + col, k->inv_scale);
+    }
+    __device__ __forceinline__ F2 shl(int q) const { return mk2(at(q, Ac - 1), at(q, Ac)); }
+    __device__ __forceinline__ F2 shr(int q) const { return mk2(at(q, Ac + 1), at(q, Ac + 2)); }
 };
 template <typename S> struct OwnStage {
     const S *b;  // stage of row i
@@ -617,6 +628,16 @@ template <typename S> struct OwnStage {
     __device__ __forceinline__ float own0(int q) const { return LoadScaled<S>::one(b + q * TmaGeom<S>::cols + cA, is); }
     __device__ __forceinline__ float m8() const { return m8v; }
     __device__ __forceinline__ float p7() const { return p7v; }
+    __device__ __forceinline__ F2 shl(int q) const
+    {
+        const S *p = b + q * TmaGeom<S>::cols + cA;
+        return mk2(LoadScaled<S>::one(p - 1, is), LoadScaled<S>::one(p, is));
+    }
+    __device__ __forceinline__ F2 shr(int q) const
+    {
+        const S *p = b + q * TmaGeom<S>::cols + cA;
+        return mk2(LoadScaled<S>::one(p + 1, is), LoadScaled<S>::one(p + 2, is));
+    }
 };
 
 // The rest of a row update once the pulled values of the pair are in fv, gv,
@@ -681,35 +702,100 @@ __device__ __forceinline__ void row_tail(const KP<float> &k, const Own &own, S *
             }
         }
     }
-    // end walls; they win in corners
+    // end walls; they win in corners.  Each node of the pair takes the rules
+    // of its own segment (a split top, Sec. 3.6); a free surface reflects f
+    // specularly (the population that left the neighbour column towards the
+    // wall, e_x reversed) and at a corner column takes the lateral side's rule
+    // for the node itself.
     if (!has_m) {
-        const int sd = 0;
-        const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
-        fv[1] = own.own(3) + sp(k.rho0 * (6.0f / 9.0f) * ux_w);
-        fv[5] = own.own(7) + sp(k.rho0 * (6.0f / 36.0f) * (ux_w + uy_w));
-        fv[8] = own.own(6) + sp(k.rho0 * (6.0f / 36.0f) * (ux_w - uy_w));
+        const int sx = end_seg(k, 0, A), sy = end_seg(k, 0, A + 1);
+        if (k.flow[sx] == 3 || k.flow[sy] == 3) {
+            const F2 o3 = own.own(3), l6 = own.shl(6), r7 = own.shr(7);
+            float c5 = 0.0f, c8x = 0.0f, c8y = 0.0f;
+            if (atA0) c5 = own.own0(7) + (k.flow[2] == 1 ? 0.0f : k.rho0 * (6.0f / 36.0f) * (k.uwx[2] + k.uwy[2]));
+            if (atAN || atBN) {
+                const F2 o6 = own.own(6);
+                const float t8 = k.rho0 * (6.0f / 36.0f) * (k.uwx[3] - k.uwy[3]);
+                c8x = o6.v.x + t8;
+                c8y = o6.v.y + t8;
+            }
+            const F2 f5 = mk2(atA0 ? c5 : l6.v.x, l6.v.y);
+            const F2 f8 = mk2(atAN ? c8x : r7.v.x, atBN ? c8y : r7.v.y);
+            const F2 w1 = own.own(3), w5 = own.own(7), w8 = own.own(6);
+            fv[1] = mk2(k.flow[sx] == 3 ? o3.v.x : w1.v.x + k.rho0 * (6.0f / 9.0f) * k.uwx[sx],
+                        k.flow[sy] == 3 ? o3.v.y : w1.v.y + k.rho0 * (6.0f / 9.0f) * k.uwx[sy]);
+            fv[5] = mk2(k.flow[sx] == 3 ? f5.v.x : w5.v.x + k.rho0 * (6.0f / 36.0f) * (k.uwx[sx] + k.uwy[sx]),
+                        k.flow[sy] == 3 ? f5.v.y : w5.v.y + k.rho0 * (6.0f / 36.0f) * (k.uwx[sy] + k.uwy[sy]));
+            fv[8] = mk2(k.flow[sx] == 3 ? f8.v.x : w8.v.x + k.rho0 * (6.0f / 36.0f) * (k.uwx[sx] - k.uwy[sx]),
+                        k.flow[sy] == 3 ? f8.v.y : w8.v.y + k.rho0 * (6.0f / 36.0f) * (k.uwx[sy] - k.uwy[sy]));
+        } else {
+            const int sd = 0;
+            const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
+            fv[1] = own.own(3) + sp(k.rho0 * (6.0f / 9.0f) * ux_w);
+            fv[5] = own.own(7) + sp(k.rho0 * (6.0f / 36.0f) * (ux_w + uy_w));
+            fv[8] = own.own(6) + sp(k.rho0 * (6.0f / 36.0f) * (ux_w - uy_w));
+        }
         const F2 og = own.own(G0 + 3), oh = own.own(H0 + 3);
-        gv[1] = mk2(scalar_bc<float>(k.swirl[sd], og.v.x, wall_psi<float>(k, sd, y2.v.x), true),
-                    scalar_bc<float>(k.swirl[sd], og.v.y, wall_psi<float>(k, sd, y2.v.y), true));
-        hv5[1] = mk2(scalar_bc<float>(k.heat[sd], oh.v.x, k.Tw[sd] - k.T0, false),
-                     scalar_bc<float>(k.heat[sd], oh.v.y, k.Tw[sd] - k.T0, false));
+        gv[1] = mk2(scalar_bc<float>(k.swirl[sx], og.v.x, wall_psi<float>(k, sx, y2.v.x), true),
+                    scalar_bc<float>(k.swirl[sy], og.v.y, wall_psi<float>(k, sy, y2.v.y), true));
+        hv5[1] = mk2(scalar_bc<float>(heat_rule(k, sx), oh.v.x, end_T(k, sx, y2.v.x) - k.T0, false),
+                     scalar_bc<float>(heat_rule(k, sy), oh.v.y, end_T(k, sy, y2.v.y) - k.T0, false));
     }
     if (!has_p) {
-        const int sd = 1;
-        const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
-        fv[3] = own.own(1) + sp(k.rho0 * (6.0f / 9.0f) * (-ux_w));
-        fv[6] = own.own(8) + sp(k.rho0 * (6.0f / 36.0f) * (-ux_w + uy_w));
-        fv[7] = own.own(5) + sp(k.rho0 * (6.0f / 36.0f) * (-ux_w - uy_w));
+        const int sx = end_seg(k, 1, A), sy = end_seg(k, 1, A + 1);
+        if (k.flow[sx] == 3 || k.flow[sy] == 3) {
+            const F2 o1 = own.own(1), l5 = own.shl(5), r8 = own.shr(8);
+            float c6 = 0.0f, c7x = 0.0f, c7y = 0.0f;
+            if (atA0) c6 = own.own0(8) + (k.flow[2] == 1 ? 0.0f : k.rho0 * (6.0f / 36.0f) * (-k.uwx[2] + k.uwy[2]));
+            if (atAN || atBN) {
+                const F2 o5 = own.own(5);
+                const float t7 = k.rho0 * (6.0f / 36.0f) * (-k.uwx[3] - k.uwy[3]);
+                c7x = o5.v.x + t7;
+                c7y = o5.v.y + t7;
+            }
+            const F2 f6 = mk2(atA0 ? c6 : l5.v.x, l5.v.y);
+            const F2 f7 = mk2(atAN ? c7x : r8.v.x, atBN ? c7y : r8.v.y);
+            const F2 w3 = own.own(1), w6 = own.own(8), w7 = own.own(5);
+            fv[3] = mk2(k.flow[sx] == 3 ? o1.v.x : w3.v.x + k.rho0 * (6.0f / 9.0f) * (-k.uwx[sx]),
+                        k.flow[sy] == 3 ? o1.v.y : w3.v.y + k.rho0 * (6.0f / 9.0f) * (-k.uwx[sy]));
+            fv[6] = mk2(k.flow[sx] == 3 ? f6.v.x : w6.v.x + k.rho0 * (6.0f / 36.0f) * (-k.uwx[sx] + k.uwy[sx]),
+                        k.flow[sy] == 3 ? f6.v.y : w6.v.y + k.rho0 * (6.0f / 36.0f) * (-k.uwx[sy] + k.uwy[sy]));
+            fv[7] = mk2(k.flow[sx] == 3 ? f7.v.x : w7.v.x + k.rho0 * (6.0f / 36.0f) * (-k.uwx[sx] - k.uwy[sx]),
+                        k.flow[sy] == 3 ? f7.v.y : w7.v.y + k.rho0 * (6.0f / 36.0f) * (-k.uwx[sy] - k.uwy[sy]));
+        } else if (sx != sy || sx == 4) {  // a split top without a free surface: per-node wall velocities
+            const F2 w3 = own.own(1), w6 = own.own(8), w7 = own.own(5);
+            fv[3] = mk2(w3.v.x + k.rho0 * (6.0f / 9.0f) * (-k.uwx[sx]), w3.v.y + k.rho0 * (6.0f / 9.0f) * (-k.uwx[sy]));
+            fv[6] = mk2(w6.v.x + k.rho0 * (6.0f / 36.0f) * (-k.uwx[sx] + k.uwy[sx]),
+                        w6.v.y + k.rho0 * (6.0f / 36.0f) * (-k.uwx[sy] + k.uwy[sy]));
+            fv[7] = mk2(w7.v.x + k.rho0 * (6.0f / 36.0f) * (-k.uwx[sx] - k.uwy[sx]),
+                        w7.v.y + k.rho0 * (6.0f / 36.0f) * (-k.uwx[sy] - k.uwy[sy]));
+        } else {
+            const int sd = 1;
+            const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
+            fv[3] = own.own(1) + sp(k.rho0 * (6.0f / 9.0f) * (-ux_w));
+            fv[6] = own.own(8) + sp(k.rho0 * (6.0f / 36.0f) * (-ux_w + uy_w));
+            fv[7] = own.own(5) + sp(k.rho0 * (6.0f / 36.0f) * (-ux_w - uy_w));
+        }
         const F2 og = own.own(G0 + 1), oh = own.own(H0 + 1);
-        gv[3] = mk2(scalar_bc<float>(k.swirl[sd], og.v.x, wall_psi<float>(k, sd, y2.v.x), true),
-                    scalar_bc<float>(k.swirl[sd], og.v.y, wall_psi<float>(k, sd, y2.v.y), true));
-        hv5[3] = mk2(scalar_bc<float>(k.heat[sd], oh.v.x, k.Tw[sd] - k.T0, false),
-                     scalar_bc<float>(k.heat[sd], oh.v.y, k.Tw[sd] - k.T0, false));
+        gv[3] = mk2(scalar_bc<float>(k.swirl[sx], og.v.x, wall_psi<float>(k, sx, y2.v.x), true),
+                    scalar_bc<float>(k.swirl[sy], og.v.y, wall_psi<float>(k, sy, y2.v.y), true));
+        hv5[3] = mk2(scalar_bc<float>(heat_rule(k, sx), oh.v.x, end_T(k, sx, y2.v.x) - k.T0, false),
+                     scalar_bc<float>(heat_rule(k, sy), oh.v.y, end_T(k, sy, y2.v.y) - k.T0, false));
     }
 
-    // central differences of the stored-state fields, with ghosts
-    const F2 uy_xm = has_m ? uy_prev : (sp(2.0f * k.uwy[0]) - pm_cur.uy);
-    const F2 uy_xp = has_p ? pm_n.uy : (sp(2.0f * k.uwy[1]) - pm_cur.uy);
+    // central differences of the stored-state fields, with ghosts (a free
+    // surface: no shear, u_y even across it)
+    F2 uy_xm = uy_prev, uy_xp = pm_n.uy;
+    if (!has_m) {
+        const int sx = end_seg(k, 0, A), sy = end_seg(k, 0, A + 1);
+        uy_xm = mk2(k.flow[sx] == 3 ? pm_cur.uy.v.x : 2.0f * k.uwy[sx] - pm_cur.uy.v.x,
+                    k.flow[sy] == 3 ? pm_cur.uy.v.y : 2.0f * k.uwy[sy] - pm_cur.uy.v.y);
+    }
+    if (!has_p) {
+        const int sx = end_seg(k, 1, A), sy = end_seg(k, 1, A + 1);
+        uy_xp = mk2(k.flow[sx] == 3 ? pm_cur.uy.v.x : 2.0f * k.uwy[sx] - pm_cur.uy.v.x,
+                    k.flow[sy] == 3 ? pm_cur.uy.v.y : 2.0f * k.uwy[sy] - pm_cur.uy.v.y);
+    }
     float lux = __shfl_up_sync(FULL, pm_cur.ux.v.y, 1), luy = __shfl_up_sync(FULL, pm_cur.uy.v.y, 1);
     float lut = __shfl_up_sync(FULL, pm_cur.ut.v.y, 1), lT = __shfl_up_sync(FULL, pm_cur.T.v.y, 1);
     float rux = __shfl_down_sync(FULL, pm_cur.ux.v.x, 1), ruy = __shfl_down_sync(FULL, pm_cur.uy.v.x, 1);

@@ -188,6 +188,44 @@ def rayleigh_benard_cylinder(nr: int = 100, nz: int = 100, Ra: float = 5e3, Pr: 
     return Case("rayleigh_benard_cylinder", params, rest_fields(nz, nr, T))
 
 
+def czochralski(nr: int = 100, nz: int = 100, beta: float = 0.4, Re_x: float = 100.0, Re_c: float = -25.0,
+                Pr: float = 0.05, Gr: float = 0.0, u_ref: float = 0.05, amp: float = 0.0, seed: int = 0,
+                T_hot: float = 1.0, T_cold: float = 0.0) -> Case:
+    """Melt flow in a rotating crucible under a rotating crystal (Sec. 3.6,
+    Wheeler's problem).
+
+    Crucible radius R_c = nr, height H = nz (alpha = H / R_c), crystal
+    radius R_x = beta R_c = top_split columns.  Re_c = R_c^2 Omega_c / nu,
+    Re_x = R_x^2 Omega_x / nu (opposite signs: counter-rotation); the larger
+    of the two wall speeds is u_ref, which fixes nu.  Boundaries as Sec. 3.6
+    prints them: axis at r = 0; crucible side wall turning with Omega_c at
+    T_hot; adiabatic bottom turning with Omega_c; the crystal (r < R_x at
+    the top) turning with Omega_x at T_cold; beyond it a free surface (no
+    normal velocity, no shear, d u_theta / dz = 0) whose temperature rises
+    linearly in r from T_cold at R_x to T_hot at R_c.  Buoyancy from the
+    Grashof number Gr = g beta dT R_c^3 / nu^2 (0: forced convection only).
+    """
+    R, H = float(nr), float(nz)
+    split = int(round(beta * nr))
+    if not 0 < split < nr:
+        raise ValueError("the crystal must cover part of the top (0 < beta nr < nr)")
+    Rx = float(split)
+    # wall speeds Omega R: crucible Re_c nu / R, crystal Re_x nu / R_x
+    nu = u_ref / max(abs(Re_c) / R, abs(Re_x) / Rx)
+    om_c, om_x = Re_c * nu / (R * R), Re_x * nu / (Rx * Rx)
+    alpha = nu / Pr
+    dT = T_hot - T_cold
+    g_beta = Gr * nu * nu / (dT * R ** 3)
+    sides = [_side(heat=SC_NEUMANN, omega=om_c), _side(heat=SC_DIRICHLET, T_w=T_cold, omega=om_x), _axis(),
+             _side(heat=SC_DIRICHLET, T_w=T_hot, omega=om_c)]
+    outer = _side(flow=FLOW_FREE, swirl=SC_NEUMANN, heat=SC_RAMP, T_w=T_hot)
+    params = {"nr": nr, "nz": nz, "r0": 0.0, "nu": nu, "alpha": alpha, "g_beta": g_beta,
+              "T0": 0.5 * (T_hot + T_cold), "rho0": 1.0, "omega3": 1.0, "omega_hi": 1.0, "sides": sides,
+              "top_split": split, "top_outer": outer}
+    T = perturbed_T(nz, nr, 0.5 * (T_hot + T_cold), amp, seed)
+    return Case("czochralski", params, rest_fields(nz, nr, T))
+
+
 def buoyancy_velocity(params: dict) -> float:
     """sqrt(g beta H dT) of a heated cylinder or annulus (dT from the
     Dirichlet walls), the velocity scale of Table 2."""

@@ -92,10 +92,30 @@ def sliding_annulus(nr, nz):
     return p
 
 
+def czochralski(nr, nz):
+    """Sec. 3.6: the top split into a rotating cold crystal and a free melt
+    surface with a temperature ramp, counter-rotating hot crucible, axis;
+    buoyancy on."""
+    c = W.czochralski(nr=max(nr, 2), nz=nz, beta=0.4 if nr >= 3 else 0.5, Re_x=200.0, Re_c=-50.0, Pr=0.7, Gr=1e4)
+    return c.params
+
+
+def free_ends_annulus(nr, nz):
+    """Free surfaces on both end walls of an annulus with porous, rotating,
+    isothermal lateral walls (the corner rules at lateral walls); buoyancy."""
+    free = W._side(flow=W.FLOW_FREE, swirl=W.SC_NEUMANN, heat=W.SC_NEUMANN)
+    sides = [dict(free), dict(free),
+             W._side(heat=W.SC_DIRICHLET, T_w=1.0, omega=0.004, u_wx=0.01, u_wy=0.003),
+             W._side(heat=W.SC_DIRICHLET, T_w=0.0, omega=-0.002, u_wx=-0.005, u_wy=0.002)]
+    return {"nr": nr, "nz": nz, "r0": 4.0, "nu": 0.06, "alpha": 0.05, "g_beta": 1e-3, "T0": 0.5,
+            "rho0": 1.0, "omega3": 1.0, "omega_hi": 1.0, "sides": sides}
+
+
 BUILDERS = {"annulus_walls": annulus_walls, "cylinder_axis": cylinder_axis,
             "periodic_annulus": periodic_annulus, "periodic_cylinder": periodic_cylinder,
             "planar_box": planar_box, "rotating_cylinder": rotating_cylinder,
-            "sliding_annulus": sliding_annulus}
+            "sliding_annulus": sliding_annulus, "czochralski": czochralski,
+            "free_ends_annulus": free_ends_annulus}
 # widths up to 128 put a wall or the axis in every 64-column window; 193 and
 # 257 leave one and two wall-free windows, where the FP32 step takes its
 # interior form of the row update
@@ -183,7 +203,8 @@ def test_fp32_fields_after_1000_steps(case):
     assert dg["T_sum"] == pytest.approx(do["T_sum"], rel=1e-6)
 
 
-@pytest.mark.parametrize("name", ["annulus_walls", "cylinder_axis", "periodic_annulus"])
+@pytest.mark.parametrize("name", ["annulus_walls", "cylinder_axis", "periodic_annulus", "czochralski",
+                                  "free_ends_annulus"])
 def test_fp64_fields_and_diagnostics_match_oracle(name):
     params = BUILDERS[name](45, 38)
     st = random_state(params, seed=11)
@@ -378,7 +399,8 @@ def _ulp16(x, mant_bits):
 
 
 @pytest.mark.parametrize("storage,mant,scale", [("fp16", 10, 1024.0), ("bf16", 7, 1.0)])
-@pytest.mark.parametrize("name", ["annulus_walls", "cylinder_axis", "periodic_annulus"])
+@pytest.mark.parametrize("name", ["annulus_walls", "cylinder_axis", "periodic_annulus", "czochralski",
+                                  "free_ends_annulus"])
 def test_16bit_distributions_after_one_step_within_one_rounding(name, storage, mant, scale):
     """One step from a state the 16-bit buffer holds exactly: every stored
     value equals the oracle's to within one stochastic rounding of its
