@@ -292,8 +292,14 @@ LB_EXPORT lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_bu
  * persistent grid, 3 = TMA ring read in place, one warp per work item; the
  * default is 3; 4 = the same with a ring of three row stages instead of
  * four, FP32 storage only: 12 instead of 10 resident warps per SM, for
- * batches whose step is one wave of work items).  LB_ERR_ARG for values out
- * of range. */
+ * batches whose step is one wave of work items; 5 = one persistent
+ * cooperative launch for all the steps of an lb_batch_step call, every work
+ * item resident (lb_batch_get_occupancy: items <= resident warps, else
+ * lb_batch_step returns LB_ERR_ARG), an item starting a step once the items
+ * around it (windows and z-segments +-1) have finished the previous one --
+ * no launch boundary between steps; each wait on a neighbour's progress is
+ * bounded (about a second) and a timeout sets the lattice's status to
+ * LB_ERR_TIMEOUT).  LB_ERR_ARG for values out of range. */
 LB_EXPORT lb_status lb_batch_set_launch(lb_batch *b, int32_t seg_rows, int32_t warps_per_block,
                                         int32_t graph_steps, int32_t row_fetch);
 /* Rows per z-segment of each lattice (seg_rows[n], in the order of

@@ -82,6 +82,7 @@ def tune_solver(solver, steps: int = 20, use_cache: bool = True) -> tuple:
 
 
 PLAN_WAVES = [1.0, 1.5, 2.0, 3.0, 4.0, 6.0]
+PERSIST_WAVES = [0.9, 1.0]
 
 
 def segment_plan(shapes: list, resident: int, waves: float, window: int = 64) -> list:
@@ -125,9 +126,15 @@ def tune_batch(batch, steps: int = 10, graph_steps: int = 10, use_cache: bool = 
     if batch.solvers[0].storage == "fp32":  # three ring stages: 12 resident warps per SM instead of 10
         plan_launches += [(4, 1, 4), (4, 2, 4)]
     cands = [(c, 0.0) for c in BATCH_CANDIDATES] + [(c, w) for c in plan_launches for w in PLAN_WAVES]
+    # one persistent launch per call: every item resident (at most one wave)
+    cands += [((4, 2, 5), w) for w in PERSIST_WAVES]
     results = []
     for launch, waves in cands:
         _apply(batch, launch, waves, 0)
+        if launch[2] == 5:
+            resident, items = batch.occupancy()
+            if items > resident:
+                continue
         batch.step(2)
         results.append((_time(batch.stream, batch.step, steps), launch, waves))
     results.sort(key=lambda r: r[0])

@@ -36,7 +36,9 @@ class Batch:
     def set_launch(self, seg_rows: int = 0, warps_per_block: int = 0, graph_steps: int = 8,
                    row_fetch: int = 0) -> None:
         """row_fetch: 0 keep, 1 plain loads, 3 TMA ring read in place, 4 the
-        same with three ring stages (FP32)."""
+        same with three ring stages (FP32), 5 one persistent launch per
+        step() call with every work item resident (neighbour progress flags
+        instead of launch boundaries)."""
         _abi.check(self.L.lb_batch_set_launch(self.h, int(seg_rows), int(warps_per_block), int(graph_steps),
                                               int(row_fetch)))
 

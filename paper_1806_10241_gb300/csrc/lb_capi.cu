@@ -649,6 +649,7 @@ struct lb_batch {
     std::vector<unsigned char> hbdiag;
     std::vector<int> hbprefix;
     bool bdiag_uploaded;
+    int *d_flags;  // progress counters of the persistent step (row fetch 5)
 };
 
 // Work queued on the lattices' own streams (initialisation, state uploads,
@@ -669,21 +670,27 @@ constexpr size_t kDiagSlot = 256;  // per lattice: its NSUM sums and status word
 
 // Batch buffer: descriptors, item prefix sums, step counter, gathered
 // diagnostics, diagnostics descriptors, diagnostics block prefix sums.
+// Work items the persistent batched step (row fetch 5) can track: one
+// progress counter each.
+constexpr int kMaxPersistItems = 16384;
+
 static size_t batch_layout(int32_t n, size_t *desc_off, size_t *prefix_off, size_t *ctl_off, size_t *diag_off,
-                           size_t *bdiag_off = nullptr, size_t *bprefix_off = nullptr)
+                           size_t *bdiag_off = nullptr, size_t *bprefix_off = nullptr, size_t *flags_off = nullptr)
 {
     const size_t d = align256((size_t)n * lbk::batch_desc_bytes());
     const size_t p = align256((size_t)(n + 1) * sizeof(int));
     const size_t t = align256(lbk::batch_ctl_bytes());
     const size_t g = align256((size_t)n * kDiagSlot);
     const size_t bd = align256((size_t)n * lbk::batch_diag_bytes());
+    const size_t bp = align256((size_t)(n + 1) * sizeof(int));
     *desc_off = 0;
     *prefix_off = d;
     *ctl_off = d + p;
     *diag_off = d + p + t;
     if (bdiag_off) *bdiag_off = d + p + t + g;
     if (bprefix_off) *bprefix_off = d + p + t + g + bd;
-    return d + p + t + g + bd + (size_t)(n + 1) * sizeof(int);
+    if (flags_off) *flags_off = d + p + t + g + bd + bp;
+    return d + p + t + g + bd + bp + (size_t)kMaxPersistItems * sizeof(int);
 }
 
 static lb_status batch_upload(lb_batch *b)
@@ -729,8 +736,8 @@ lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_buf, size_t 
 {
     if (!out || !ctxs || n < 1 || !dev_buf) return fail(nullptr, LB_ERR_ARG, "NULL argument or n < 1");
     *out = nullptr;
-    size_t doff, poff, coff, goff, bdoff, bpoff;
-    const size_t need = batch_layout(n, &doff, &poff, &coff, &goff, &bdoff, &bpoff);
+    size_t doff, poff, coff, goff, bdoff, bpoff, foff;
+    const size_t need = batch_layout(n, &doff, &poff, &coff, &goff, &bdoff, &bpoff, &foff);
     if (bytes < need) return fail(nullptr, LB_ERR_NOMEM, "batch buffer holds %zu bytes, %zu needed", bytes, need);
     if (((uintptr_t)dev_buf & 255) != 0) return fail(nullptr, LB_ERR_ARG, "dev_buf must be 256-byte aligned");
     const int storage = ctxs[0] ? ctxs[0]->hp.storage : -1;
@@ -758,6 +765,7 @@ lb_status lb_batch_create(lb_ctx *const *ctxs, int32_t n, void *dev_buf, size_t 
     b->hdiag.assign((size_t)n * kDiagSlot, 0);
     b->d_bdiag = b->buf + bdoff;
     b->d_bprefix = (int *)(b->buf + bpoff);
+    b->d_flags = (int *)(b->buf + foff);
     b->bdiag_uploaded = false;
     b->stream = (cudaStream_t)cuda_stream;
     b->seg_rows = 4;
@@ -796,9 +804,9 @@ lb_status lb_batch_set_launch(lb_batch *b, int32_t seg_rows, int32_t warps_per_b
                               int32_t row_fetch)
 {
     if (!b || seg_rows < 0 || warps_per_block < 0 || warps_per_block > 8 || graph_steps < 0 ||
-        !(row_fetch == 0 || row_fetch == 1 || row_fetch == 3 || row_fetch == 4))
+        !(row_fetch == 0 || row_fetch == 1 || row_fetch == 3 || row_fetch == 4 || row_fetch == 5))
         return fail(nullptr, LB_ERR_ARG,
-                    "seg_rows >= 0, 0 <= warps_per_block <= 8, graph_steps >= 0, row_fetch 0, 1, 3 or 4");
+                    "seg_rows >= 0, 0 <= warps_per_block <= 8, graph_steps >= 0, row_fetch 0, 1, 3, 4 or 5");
     if (row_fetch == 4 && b->storage != LB_FP32)
         return fail(nullptr, LB_ERR_ARG, "row_fetch 4 (three ring stages) is for FP32 storage");
     if (row_fetch) b->row_fetch = row_fetch;
@@ -842,6 +850,27 @@ lb_status lb_batch_step(lb_batch *b, int32_t nsteps)
     {
         cudaError_t e = batch_streams_wait(b, true);
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch stream order");
+    }
+    if (b->row_fetch == 5 && nsteps > 0) {  // one persistent launch for all the steps
+        int resident = 0;
+        cudaError_t e = lbk::batch_resident_warps(b->storage, 5, b->wpb, &resident);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "occupancy");
+        if (b->total > resident || b->total > kMaxPersistItems)
+            return fail(nullptr, LB_ERR_ARG,
+                        "row fetch 5 needs every work item resident: %d items, %d resident warps (at most %d items)",
+                        b->total, resident, kMaxPersistItems);
+        e = lbk::launch_batch_persist(b->storage, b->d_desc, b->d_prefix, (int)b->ctxs.size(), b->total, b->wpb,
+                                      b->counter, nsteps, b->d_flags, b->stream);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "persistent batch launch");
+        b->counter += (unsigned long long)nsteps;
+        for (size_t m = 0; m < b->ctxs.size(); ++m) {
+            lb_ctx *c = b->ctxs[m];
+            c->step = (int64_t)(b->step0[m] + b->counter);
+            c->cur = (int)((b->parity0[m] + b->counter) & 1ULL);
+        }
+        e = batch_streams_wait(b, false);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch stream order");
+        return LB_OK;
     }
     int32_t left = nsteps;
     unsigned long long t = b->counter;  // batch step of the next launch

@@ -116,6 +116,11 @@ cudaError_t batch_prepare(int storage);
 cudaError_t launch_batch(int storage, int row_fetch, const void *desc, const int *prefix, int n, int total,
                          void *ctl, int wpb, int blocks, unsigned long long t0, int from_counter,
                          cudaStream_t s);
+// nsteps batch steps t0 .. t0 + nsteps - 1 in one cooperative launch (every
+// work item resident; items wait only for their neighbours' progress in
+// done[total], cleared here first).
+cudaError_t launch_batch_persist(int storage, const void *desc, const int *prefix, int n, int total, int wpb,
+                                 unsigned long long t0, int nsteps, int *done, cudaStream_t s);
 // The device counter of a batch: set to value, or advanced by it (add != 0).
 cudaError_t launch_batch_counter(void *ctl, unsigned long long value, int add, cudaStream_t s);
 // Batched diagnostics: one descriptor per lattice (its partial-sum buffer and

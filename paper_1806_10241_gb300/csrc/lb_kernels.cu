@@ -1394,6 +1394,121 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restric
     }
 }
 
+// The batched step as one persistent launch for nsteps steps, for batches
+// whose work items all fit on the device at once (a cooperative launch, one
+// warp per item).  Instead of a launch boundary after each step, an item
+// starts step j once the up-to-eight items around it (windows and z-segments
+// +-1 in its lattice; segments wrap on a periodic lattice) have completed
+// step j - 1: their halo rows and columns are then written (read after write)
+// and no longer read from the buffer that step j overwrites (write after
+// read).  done[item] counts the steps an item has completed in this launch,
+// stored with release semantics after its writes; lanes 0..7 poll one
+// neighbour each with acquire loads, at most kFlagWaitLimit times with a
+// short sleep between polls (about a second), after which the lattice's
+// status word gets LB_ERR_TIMEOUT and the warp leaves.
+constexpr int kFlagWaitLimit = 1 << 20;
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <typename S, int R>
+__global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3p(const BatchDesc *__restrict__ d, const int *__restrict__ prefix,
+                                                       int n, int total, unsigned long long t0, int nsteps, int *done)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    unsigned char *ring = smem + batch3_ring_bytes<S, R>() * wib;
+    KP<float> *skp = reinterpret_cast<KP<float> *>(smem + batch3_ring_bytes<S, R>() * wpb);
+    const int item = blockIdx.x * wpb + wib;
+    if (item >= total) return;
+    const int lo = batch_instance(prefix, n, item, lane);
+    const BatchDesc *bd = d + lo;
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&bd->k);
+        uint32_t *o = reinterpret_cast<uint32_t *>(&skp[wib]);
+        for (int q = lane; q < (int)(sizeof(KP<float>) / 4); q += 32) o[q] = src[q];
+    }
+    __syncwarp();
+    const KP<float> &k = skp[wib];
+    const int local = item - prefix[lo];
+    const int nw2 = bd->nwin2;
+    const int w = local % nw2, sg = local / nw2;
+    const int seg = bd->seg_rows, nseg = (k.nz + seg - 1) / seg;
+    const int s = sg * seg, e = min(k.nz, s + seg);
+    const bool has_m = s > 0 || k.xper, has_last = e < k.nz || k.xper;
+    // the neighbour item this lane watches (lanes 0..7), -1 for none
+    int nb = -1;
+    if (lane < 8) {
+        const int c = lane < 4 ? lane : lane + 1;  // the 3 x 3 block without its centre
+        const int dw = c % 3 - 1, dg = c / 3 - 1;
+        const int w2 = w + dw;
+        int g2 = sg + dg;
+        if (k.xper) g2 = (g2 + nseg) % nseg;
+        if (w2 >= 0 && w2 < nw2 && g2 >= 0 && g2 < nseg && g2 * nw2 + w2 != local) nb = prefix[lo] + g2 * nw2 + w2;
+    }
+    if (lane < 2)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((unsigned long long)bd->map[lane])
+                     : "memory");
+    RowRing<S, R> rs;
+    rs.ring = ring;
+    rs.ring_s = smem_u32(ring);
+    rs.bar_s = smem_u32(ring + TmaGeom<S>::box_bytes);
+    rs.bar_stride = TmaGeom<S>::stage_bytes;
+    rs.first = has_m ? s - 1 : s;
+    rs.nrows = (e - s) + (has_m ? 1 : 0) + (has_last ? 1 : 0);
+    rs.nz = k.nz;
+    rs.x0 = w * 64 - TmaGeom<S>::off;
+    rs.lane = lane;
+    rs.status = bd->status;
+    for (int j = 0; j < nsteps; ++j) {
+        if (j > 0) {
+            bool ok = true;
+            if (nb >= 0) {
+                int it = 0;
+                while (ld_acquire_gpu(done + nb) < j) {
+                    if (++it > kFlagWaitLimit) {
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+            if (!__all_sync(FULL, ok)) {
+                if (lane == 0) atomicExch(bd->status, (int)LB_ERR_TIMEOUT);
+                return;
+            }
+            // the neighbours' writes, acquired by the watching lanes, before this
+            // warp's bulk-tensor reads; the ring stages read by the last step
+            // before the copies that refill them
+            __threadfence();
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        const unsigned long long t = t0 + (unsigned long long)j;
+        const int cur = (bd->parity0 + (int)(t & 1ULL)) & 1;
+        rs.map = reinterpret_cast<const CUtensorMap *>(bd->map[cur]);
+        if (j == 0) rs.start();  // the barriers, once
+        else rs.prime();
+        march3<S, R, false, true>(k, (const S *)bd->buf[cur], (S *)bd->buf[cur ^ 1], w * 64, s, e,
+                                  salt_of(bd->step0 + t), rs);
+        if (*(volatile const int *)bd->status != 0) return;  // a ring wait ran out
+        rs.advance();
+        // publish: this item's writes, then its progress
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_gpu(done + item, j + 1);
+    }
+}
+
 // Diagnostics of every lattice of a batch in three launches instead of three
 // per lattice: the blocks of all the lattices' diagnostics grids in one grid,
 // then one final-reduction block and one wall-flux block per lattice.  Each
@@ -1770,16 +1885,28 @@ cudaError_t batch_prepare(int storage)
         case ST_FP32: {
             cudaError_t e = cudaFuncSetAttribute(k_batch3<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)batch3_smem_bytes<float, 4>(8));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_batch3p<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batch3_smem_bytes<float, 3>(8));
             if (e != cudaSuccess) return e;
             return cudaFuncSetAttribute(k_batch3<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)batch3_smem_bytes<float, 3>(8));
         }
-        case ST_FP16:
+        case ST_FP16: {
+            cudaError_t e = cudaFuncSetAttribute(k_batch3p<__half, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)batch3_smem_bytes<__half>(8));
+            if (e != cudaSuccess) return e;
             return cudaFuncSetAttribute(k_batch3<__half, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)batch3_smem_bytes<__half>(8));
-        case ST_BF16:
+        }
+        case ST_BF16: {
+            cudaError_t e = cudaFuncSetAttribute(k_batch3p<__nv_bfloat16, 4>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)batch3_smem_bytes<__nv_bfloat16>(8));
+            if (e != cudaSuccess) return e;
             return cudaFuncSetAttribute(k_batch3<__nv_bfloat16, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)batch3_smem_bytes<__nv_bfloat16>(8));
+        }
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1810,6 +1937,25 @@ cudaError_t batch_resident_warps(int storage, int row_fetch, int wpb, int *out)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = batch_prepare(storage);
     if (e != cudaSuccess) return e;
+    if (row_fetch == 5) {
+        switch (storage) {
+            case ST_FP32:
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch3p<float, 3>, 32 * wpb,
+                                                                  batch3_smem_bytes<float, 3>(wpb));
+                break;
+            case ST_FP16:
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch3p<__half, 4>, 32 * wpb,
+                                                                  batch3_smem_bytes<__half>(wpb));
+                break;
+            case ST_BF16:
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch3p<__nv_bfloat16, 4>, 32 * wpb,
+                                                                  batch3_smem_bytes<__nv_bfloat16>(wpb));
+                break;
+            default: return cudaErrorInvalidValue;
+        }
+        *out = sms * per * wpb;
+        return e;
+    }
     switch (storage) {
         case ST_FP32:
             if (row_fetch == 4)
@@ -1831,6 +1977,30 @@ cudaError_t batch_resident_warps(int storage, int row_fetch, int wpb, int *out)
     }
     *out = sms * per * wpb;
     return e;
+}
+
+cudaError_t launch_batch_persist(int storage, const void *desc, const int *prefix, int n, int total, int wpb,
+                                 unsigned long long t0, int nsteps, int *done, cudaStream_t s)
+{
+    if (total < 1 || nsteps < 1) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(done, 0, (size_t)total * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const BatchDesc *dd = (const BatchDesc *)desc;
+    void *args[] = {(void *)&dd, (void *)&prefix, (void *)&n, (void *)&total, (void *)&t0, (void *)&nsteps,
+                    (void *)&done};
+    const dim3 grid((total + wpb - 1) / wpb), block(32 * wpb);
+    switch (storage) {
+        case ST_FP32:
+            return cudaLaunchCooperativeKernel((const void *)k_batch3p<float, 3>, grid, block, args,
+                                               batch3_smem_bytes<float, 3>(wpb), s);
+        case ST_FP16:
+            return cudaLaunchCooperativeKernel((const void *)k_batch3p<__half, 4>, grid, block, args,
+                                               batch3_smem_bytes<__half>(wpb), s);
+        case ST_BF16:
+            return cudaLaunchCooperativeKernel((const void *)k_batch3p<__nv_bfloat16, 4>, grid, block, args,
+                                               batch3_smem_bytes<__nv_bfloat16>(wpb), s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_batch_counter(void *ctl, unsigned long long value, int add, cudaStream_t s)

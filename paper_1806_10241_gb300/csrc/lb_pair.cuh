@@ -983,12 +983,17 @@ template <typename S, int R> struct RowRing {
     uint32_t bar_stride;        // bytes between consecutive barriers
     int first, nrows, nz, x0, lane, waited, issued;
     int *status;
+    // Sequence number of row 0 of the current march: a warp that marches
+    // several times through one ring (one time step after another) keeps its
+    // barriers, initialised once, and continues their phases instead of
+    // initialising them again (which a valid mbarrier does not allow).
+    int base = 0;
 
     __device__ __forceinline__ void issue(int t)
     {
         int row = first + t;
         row = row >= nz ? row - nz : (row < 0 ? row + nz : row);
-        const int st = t % R;
+        const int st = (base + t) % R;
         const uint32_t bar = bar_s + bar_stride * st, dst = ring_s + (uint32_t)(TmaGeom<S>::stage_bytes * st);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
                      "r"((uint32_t)TmaGeom<S>::box_bytes)
@@ -1002,20 +1007,31 @@ template <typename S, int R> struct RowRing {
 
     __device__ __forceinline__ void start()
     {
-        waited = 0;
-        issued = nrows < R ? nrows : R;
         if (lane == 0) {
             for (int s = 0; s < R; ++s)
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s + bar_stride * s) : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            for (int t = 0; t < issued; ++t) issue(t);
         }
+        prime();
+    }
+
+    // the first copies of a march (barriers already initialised)
+    __device__ __forceinline__ void prime()
+    {
+        waited = 0;
+        issued = nrows < R ? nrows : R;
+        if (lane == 0)
+            for (int t = 0; t < issued; ++t) issue(t);
         __syncwarp();
     }
 
+    // the next march through the same ring continues the sequence
+    __device__ __forceinline__ void advance() { base += nrows; }
+
     __device__ __forceinline__ bool wait_one(int t)
     {
-        return mbar_wait_bounded(bar_s + bar_stride * (t % R), (uint32_t)((t / R) & 1), kTmaWaitLimit);
+        const int q = base + t;
+        return mbar_wait_bounded(bar_s + bar_stride * (q % R), (uint32_t)((q / R) & 1), kTmaWaitLimit);
     }
 
     // rows up to sequence index t have landed (false after a timeout, with
@@ -1039,7 +1055,7 @@ template <typename S, int R> struct RowRing {
 
     __device__ __forceinline__ const S *stage(int t) const
     {
-        return reinterpret_cast<const S *>(ring + TmaGeom<S>::stage_bytes * (t % R));
+        return reinterpret_cast<const S *>(ring + TmaGeom<S>::stage_bytes * ((base + t) % R));
     }
 
     // every lane is done with row t: its stage takes row t + R

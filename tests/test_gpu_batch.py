@@ -42,7 +42,7 @@ def test_batch_equals_individual_runs(storage, row_fetch):
         s = Solver(c.params, storage=storage, stream=stream)
         s.set_launch(0, 0, row_fetch)
         s.init_fields(c.fields)
-        s.step(49)
+        s.step(56)
         alone.append(s.get_dist())
     mixed = []
     for c in cases:
@@ -66,9 +66,15 @@ def test_batch_equals_individual_runs(storage, row_fetch):
         b.step(5)
     else:
         b.step(5)
+    # one persistent launch per call, items waiting on their neighbours' progress
+    b.set_launch(seg_rows=3, warps_per_block=2, graph_steps=0, row_fetch=5)
+    resident, items = b.occupancy()
+    assert items <= resident
+    b.step(6)
+    b.step(1)
     torch.cuda.synchronize()
     for c, a, s in zip(cases, alone, mixed):
-        assert s.step_count == 49
+        assert s.step_count == 56
         assert np.array_equal(s.get_dist(), a), c.name
     b.close()
 
@@ -187,4 +193,44 @@ def test_segment_plan_rejects_out_of_range_values():
     resident, items = b.occupancy()
     assert resident >= 152 and items > 0
     assert r4 > resident  # three stages: more warps resident
+    b.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_persistent_batch_equals_launch_per_step(storage):
+    """Row fetch 5 (one cooperative launch for all the steps of a call) gives
+    the bits of one launch per step, over a long call on uneven lattices with
+    a periodic one among them (z-segments that wrap)."""
+    from paper_1806_10241_gb300.batch import Batch
+    from paper_1806_10241_gb300.solver import Solver
+    cases = _cases()
+    runs = []
+    for fetch in (3, 5):
+        stream = torch.cuda.Stream()
+        sols = []
+        for c in cases:
+            s = Solver(c.params, storage=storage, stream=stream)
+            s.init_fields(c.fields)
+            sols.append(s)
+        b = Batch(sols, stream=stream, seg_rows=5, warps_per_block=2, graph_steps=0, row_fetch=fetch)
+        b.step(150)
+        torch.cuda.synchronize()
+        assert all(d["status"] == 0 for d in b.diag())
+        runs.append([s.get_dist() for s in sols])
+        b.close()
+    for c, a, p in zip(cases, runs[0], runs[1]):
+        assert np.array_equal(a, p), c.name
+
+
+def test_persistent_batch_rejects_more_items_than_resident_warps():
+    from paper_1806_10241_gb300._abi import LBError
+    from paper_1806_10241_gb300.batch import Batch
+    from paper_1806_10241_gb300.solver import Solver
+    c = W.swirling_cylinder(nr=1024, nz=2048, amp=0.0)
+    s = Solver(c.params, storage="fp32")
+    b = Batch([s], stream=torch.cuda.Stream(), seg_rows=4, row_fetch=5)
+    resident, items = b.occupancy()
+    assert items > resident
+    with pytest.raises(LBError):
+        b.step(1)
     b.close()
