@@ -108,6 +108,25 @@ def test_create_and_parameter_validation_without_device_work(lib):
         bad["sides"][0]["flow"] = W.FLOW_PERIODIC  # only one end periodic
         assert lib.lb_set_params(ctx, C.byref(_abi.make_params(bad))) == _abi.LB_ERR_ARG
         assert b"periodic" in lib.lb_last_error(ctx)
+        # the Czochralski family (Sec. 3.6): a free surface only on an end wall, the
+        # ramp only on the top's outer segment, the split inside the lattice
+        bad = dict(case.params)
+        bad["sides"] = [dict(s) for s in case.params["sides"]]
+        bad["sides"][3]["flow"] = W.FLOW_FREE
+        assert lib.lb_set_params(ctx, C.byref(_abi.make_params(bad))) == _abi.LB_ERR_ARG
+        assert b"free surface" in lib.lb_last_error(ctx)
+        bad = dict(case.params)
+        bad["sides"] = [dict(s) for s in case.params["sides"]]
+        bad["sides"][1]["heat"] = W.SC_RAMP
+        assert lib.lb_set_params(ctx, C.byref(_abi.make_params(bad))) == _abi.LB_ERR_ARG
+        assert b"ramp" in lib.lb_last_error(ctx)
+        cz = W.czochralski(nr=16, nz=32)
+        for key, val in (("top_split", 16), ("top_split", -1)):
+            assert lib.lb_set_params(ctx, C.byref(_abi.make_params(dict(cz.params, **{key: val})))) == _abi.LB_ERR_ARG
+        outer = dict(cz.params["top_outer"], flow=W.FLOW_AXIS)
+        assert lib.lb_set_params(ctx, C.byref(_abi.make_params(dict(cz.params, top_outer=outer)))) == _abi.LB_ERR_ARG
+        outer = dict(cz.params["top_outer"], T_w=float("nan"))
+        assert lib.lb_set_params(ctx, C.byref(_abi.make_params(dict(cz.params, top_outer=outer)))) == _abi.LB_ERR_ARG
         assert lib.lb_set_launch(ctx, 16, 9, 0) == _abi.LB_ERR_ARG
         assert lib.lb_set_launch(ctx, 16, 4, 4) == _abi.LB_ERR_ARG
         seg, wpb, fetch = C.c_int32(), C.c_int32(), C.c_int32()
