@@ -761,18 +761,33 @@ __global__ void __maxnreg__(255) k_step64(KP<C> k, const S *__restrict__ src, S 
     step_body<S, C>(k, src, dst, seg_rows, nwin);
 }
 
+// Block of a step grid in traversal order: every other step (rev = 1) the
+// blocks take the lattice from its last row segment back to its first.  A step
+// then starts on the rows the previous step wrote last, which are still in
+// the L2 (129 MB against the 319 MB of the 1024 x 2048 FP32 lattice); the
+// results do not depend on the order.
+__device__ __forceinline__ void step_block(int rev, int &bx, int &by)
+{
+    const unsigned nb = gridDim.x * gridDim.y, b0 = blockIdx.y * gridDim.x + blockIdx.x;
+    const unsigned b = rev ? nb - 1u - b0 : b0;
+    bx = (int)(b % gridDim.x);
+    by = (int)(b / gridDim.x);
+}
+
 // FP32-compute step on column pairs (lb_pair.cuh): 64 aligned columns per warp
 #ifndef LB_STEP2_MAXREG
 #define LB_STEP2_MAXREG 232
 #endif
 template <typename S>
 __global__ void __maxnreg__(LB_STEP2_MAXREG) k_step2(KP<float> k, const S *__restrict__ src, S *__restrict__ dst,
-                                                     int seg_rows, int nwin2, uint32_t salt)
+                                                     int seg_rows, int nwin2, uint32_t salt, int rev)
 {
-    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int bx, by;
+    step_block(rev, bx, by);
+    const int warp = bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (warp >= nwin2) return;
     const int lane = threadIdx.x & 31;
-    const int s = blockIdx.y * seg_rows;
+    const int s = by * seg_rows;
     const int e = min(k.nz, s + seg_rows);
     const int A = warp * 64 + 2 * lane;
     const int Amax = (k.nr - 1) & ~1;
@@ -790,14 +805,16 @@ __global__ void __maxnreg__(LB_STEP2_MAXREG) k_step2(KP<float> k, const S *__res
 template <typename S>
 __global__ void __maxnreg__(LB_STEP2_MAXREG)
     k_step2_tma(KP<float> k, const __grid_constant__ CUtensorMap map, const S *__restrict__ src,
-                S *__restrict__ dst, int seg_rows, int nwin2, uint32_t salt, int *status)
+                S *__restrict__ dst, int seg_rows, int nwin2, uint32_t salt, int *status, int rev)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int wib = threadIdx.x >> 5;
-    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+    int bx, by;
+    step_block(rev, bx, by);
+    const int warp = bx * (blockDim.x >> 5) + wib;
     if (warp >= nwin2) return;
     const int lane = threadIdx.x & 31;
-    const int s = blockIdx.y * seg_rows;
+    const int s = by * seg_rows;
     const int e = min(k.nz, s + seg_rows);
     const bool has_m = s > 0 || k.xper, has_last = e < k.nz || k.xper;
     const int nrows = (e - s) + (has_m ? 1 : 0) + (has_last ? 1 : 0);
@@ -846,14 +863,16 @@ __host__ __device__ size_t ring_smem_bytes(int wpb)
 template <typename S>
 __global__ void __maxnreg__(LB_STEP3_MAXREG)
     k_step3_tma(KP<float> k, const __grid_constant__ CUtensorMap map, const S *__restrict__ src,
-                S *__restrict__ dst, int seg_rows, int nwin2, uint32_t salt, int *status)
+                S *__restrict__ dst, int seg_rows, int nwin2, uint32_t salt, int *status, int rev)
 {
     constexpr int R = kRingStages<S>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int wib = threadIdx.x >> 5;
-    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+    int bx, by;
+    step_block(rev, bx, by);
+    const int warp = bx * (blockDim.x >> 5) + wib;
     if (warp >= nwin2) return;
-    const int s = blockIdx.y * seg_rows;
+    const int s = by * seg_rows;
     const int e = min(k.nz, s + seg_rows);
     const bool has_m = s > 0 || k.xper, has_last = e < k.nz || k.xper;
     const int per_warp = R * TmaGeom<S>::stage_bytes + 128;  // keeps every ring 128-byte aligned
@@ -1337,7 +1356,7 @@ __host__ __device__ size_t batch3_smem_bytes(int wpb)
 template <typename S, int R>
 __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restrict__ d, const int *__restrict__ prefix,
                                                       int n, int total, const BatchCtl *ctl, unsigned long long t0,
-                                                      int from_counter)
+                                                      int from_counter, int rev)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1350,8 +1369,9 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restric
     // so they overlap the previous launch's last blocks; the step counter and
     // the rows are read after the wait below.
     grid_dependency_trigger();
-    const int item = blockIdx.x * wpb + wib;
-    if (item < total) {
+    const int item0 = blockIdx.x * wpb + wib;
+    const int item = rev ? total - 1 - item0 : item0;  // every other step from the last item back
+    if (item0 < total) {
         const int lo = batch_instance(prefix, n, item, lane);
         const BatchDesc *bd = d + lo;
         {
@@ -1647,7 +1667,7 @@ cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *
             cudaLaunchAttribute pdl[1];
             pdl_config(cfg, pdl, grid, dim3(32 * wpb), sm, s);
             e = cudaLaunchKernelEx(&cfg, k_step3_tma<S>, k, *(const CUtensorMap *)tmap, (const S *)src, (S *)dst,
-                                   seg, nwin2, step_salt(step), status);
+                                   seg, nwin2, step_salt(step), status, (int)(step & 1ULL));
             if (e != cudaSuccess) return e;
         } else if (tmap && l.use_tma) {
             const size_t sm = tma_smem_bytes<S>(wpb);
@@ -1658,14 +1678,14 @@ cudaError_t step_t(const HostParams &h, const Launch &l, const void *src, void *
             cudaLaunchAttribute pdl[1];
             pdl_config(cfg, pdl, grid, dim3(32 * wpb), sm, s);
             e = cudaLaunchKernelEx(&cfg, k_step2_tma<S>, k, *(const CUtensorMap *)tmap, (const S *)src, (S *)dst,
-                                   seg, nwin2, step_salt(step), status);
+                                   seg, nwin2, step_salt(step), status, (int)(step & 1ULL));
             if (e != cudaSuccess) return e;
         } else {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute pdl[1];
             pdl_config(cfg, pdl, grid, dim3(32 * wpb), 0, s);
             cudaError_t e = cudaLaunchKernelEx(&cfg, k_step2<S>, k, (const S *)src, (S *)dst, seg, nwin2,
-                                               step_salt(step));
+                                               step_salt(step), (int)(step & 1ULL));
             if (e != cudaSuccess) return e;
         }
     }
@@ -2016,6 +2036,9 @@ cudaError_t launch_batch(int storage, int row_fetch, const void *desc, const int
     if (need < 1) return cudaSuccess;
     const BatchDesc *dd = (const BatchDesc *)desc;
     const BatchCtl *cc = (const BatchCtl *)ctl;
+    // the item order alternates with the step (inside a graph with the launch
+    // index, t0 = j there): a step starts on the items the previous one wrote last
+    const int rev = (int)(t0 & 1ULL);
     if (row_fetch == 3 || row_fetch == 4) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute pdl[1];
@@ -2023,17 +2046,17 @@ cudaError_t launch_batch(int storage, int row_fetch, const void *desc, const int
             case ST_FP32:
                 if (row_fetch == 4) {
                     pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), batch3_smem_bytes<float, 3>(wpb), s);
-                    return cudaLaunchKernelEx(&cfg, k_batch3<float, 3>, dd, prefix, n, total, cc, t0, from_counter);
+                    return cudaLaunchKernelEx(&cfg, k_batch3<float, 3>, dd, prefix, n, total, cc, t0, from_counter, rev);
                 }
                 pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), batch3_smem_bytes<float, 4>(wpb), s);
-                return cudaLaunchKernelEx(&cfg, k_batch3<float, 4>, dd, prefix, n, total, cc, t0, from_counter);
+                return cudaLaunchKernelEx(&cfg, k_batch3<float, 4>, dd, prefix, n, total, cc, t0, from_counter, rev);
             case ST_FP16:
                 pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), batch3_smem_bytes<__half>(wpb), s);
-                return cudaLaunchKernelEx(&cfg, k_batch3<__half, 4>, dd, prefix, n, total, cc, t0, from_counter);
+                return cudaLaunchKernelEx(&cfg, k_batch3<__half, 4>, dd, prefix, n, total, cc, t0, from_counter, rev);
             case ST_BF16:
                 pdl_config(cfg, pdl, dim3(need), dim3(32 * wpb), batch3_smem_bytes<__nv_bfloat16>(wpb), s);
                 return cudaLaunchKernelEx(&cfg, k_batch3<__nv_bfloat16, 4>, dd, prefix, n, total, cc, t0,
-                                          from_counter);
+                                          from_counter, rev);
             default: return cudaErrorInvalidValue;
         }
     }
