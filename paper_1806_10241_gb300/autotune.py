@@ -121,7 +121,11 @@ def tune_batch(batch, steps: int = 10, graph_steps: int = 10, use_cache: bool = 
     if key in cache and len(cache[key].get("launch", [])) == 3 and "waves" in cache[key]:
         best = tuple(cache[key]["launch"]) + (cache[key]["waves"],)
         _apply(batch, best[:3], best[3], graph_steps)
-        return best
+        resident, items = batch.occupancy()
+        if best[2] != 5 or items <= resident:
+            return best
+        # a persistent launch chosen for another batch of this size class
+        # does not fit this one: tune it afresh
     plan_launches = [(4, 1, 3), (4, 2, 3)]
     if batch.solvers[0].storage == "fp32":  # three ring stages: 12 resident warps per SM instead of 10
         plan_launches += [(4, 1, 4), (4, 2, 4)]

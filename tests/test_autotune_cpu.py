@@ -58,3 +58,42 @@ def test_segment_plan_balances_items_and_fills_the_waves():
             assert 1 <= seg <= nz
     # one lattice far smaller than the item length keeps a single segment
     assert autotune.segment_plan([(64, 8), (1024, 2048)], 152, 1.0)[0] == 8
+
+
+class FakeBatch:
+    """The Batch surface tune_batch uses, with a fixed occupancy."""
+
+    def __init__(self, resident, items):
+        self.solvers = [FakeSolver("fp32", 64, 64)]
+        self.nodes = 4096
+        self.resident, self.items = resident, items
+        self.launches, self.segments, self.steps = [], [], 0
+        self.stream = None
+
+    def set_launch(self, *a):
+        self.launches.append(a)
+
+    def set_segments(self, seg):
+        self.segments.append(seg)
+
+    def occupancy(self):
+        return self.resident, self.items
+
+    def step(self, n=1):
+        self.steps += n
+
+
+def test_cached_persistent_batch_launch_is_rechecked(tmp_path, monkeypatch):
+    """A cached persistent launch (row fetch 5) is applied only when every work
+    item of this batch is resident; otherwise the batch is tuned afresh."""
+    path = tmp_path / "autotune.json"
+    monkeypatch.setattr(autotune, "_CACHE", str(path))
+    key = f"batch/fp32/{autotune._size_class(4096)}/{autotune._size_class(1)}"
+    path.write_text(json.dumps({key: {"launch": [4, 2, 5], "waves": 1.0, "ms_per_step": 0.01}}))
+    fits = FakeBatch(resident=100, items=50)
+    assert autotune.tune_batch(fits) == (4, 2, 5, 1.0) and fits.steps == 0
+    timed = []
+    monkeypatch.setattr(autotune, "_time", lambda stream, fn, steps: timed.append(1) or 1.0)
+    too_many = FakeBatch(resident=100, items=150)
+    best = autotune.tune_batch(too_many)
+    assert timed and best[2] != 5  # tuned again, and no persistent candidate could run
