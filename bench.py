@@ -50,10 +50,13 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the step kernels' sources and the nvcc flags they are built with."""
+    from paper_1806_10241_gb300.build import FLAGS
     h = hashlib.sha256()
     for name in ("lb_kernels.cu", "lb_internal.h", "lb_pair.cuh"):
         with open(os.path.join(ROOT, "paper_1806_10241_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
+    h.update(" ".join(FLAGS).encode())
     return h.hexdigest()[:16]
 
 

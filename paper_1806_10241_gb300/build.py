@@ -18,7 +18,13 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbaxi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
-FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+# -fmad=false: no a * b + c in the scalar code (wall rules, ghosts, halo
+# fields) is contracted into an FMA behind the source's back.  Whether the
+# compiler contracts depends on the inlining context, so the same rule could
+# round differently in the single-lattice and the batched kernels, or with
+# plain loads and the TMA ring.  The node update spells its FMAs out
+# (packed FP32x2 intrinsics) and is unaffected.
+FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]
 
 

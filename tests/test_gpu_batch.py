@@ -79,6 +79,57 @@ def test_batch_equals_individual_runs(storage, row_fetch):
     b.close()
 
 
+# every boundary family of the single-lattice parity tests, at widths of one
+# and two 64-column windows and heights that split into uneven segments
+FAMILY_SHAPES = {"annulus_walls": (65, 23), "cylinder_axis": (33, 17), "periodic_annulus": (97, 12),
+                 "periodic_cylinder": (128, 9), "planar_box": (7, 9), "rotating_cylinder": (61, 13),
+                 "sliding_annulus": (70, 8), "czochralski": (40, 31), "free_ends_annulus": (100, 20)}
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_batch_of_every_boundary_family_equals_individual_runs(storage):
+    """Lattices of every boundary family (walls sliding, porous and rotating,
+    the axis, periodic ends, the planar form, rigid rotation, the Czochralski
+    split top with a free surface and the surface ramp, free surfaces at both
+    ends) from seeded random states, batched together through each launch
+    path, give the bits of the single-lattice step."""
+    from test_gpu_parity import BUILDERS, random_state
+    from paper_1806_10241_gb300.batch import Batch
+    from paper_1806_10241_gb300.solver import Solver
+    stream = torch.cuda.Stream()
+    params = [BUILDERS[name](*shape) for name, shape in FAMILY_SHAPES.items()]
+    states = [random_state(p, seed) for seed, p in enumerate(params)]
+    alone = []
+    for p, st in zip(params, states):
+        s = Solver(p, storage=storage, stream=stream)
+        s.set_dist(st)
+        s.step(40)
+        alone.append(s.get_dist())
+    sols = []
+    for p, st in zip(params, states):
+        s = Solver(p, storage=storage, stream=stream)
+        s.set_dist(st)
+        sols.append(s)
+    b = Batch(sols, stream=stream, graph_steps=4)
+    b.step(9)  # TMA ring, graphs of 4 launches and one launch outside
+    b.set_launch(seg_rows=5, warps_per_block=2, graph_steps=0, row_fetch=1)
+    b.step(7)  # plain loads
+    b.set_segments([3, 0, 2, 9, 1, 13, 4, 6, 5])
+    b.set_launch(seg_rows=4, warps_per_block=1, graph_steps=3, row_fetch=4 if storage == "fp32" else 3)
+    b.step(8)
+    b.set_segments(None)
+    b.set_launch(seg_rows=3, warps_per_block=2, graph_steps=0, row_fetch=5)
+    resident, items = b.occupancy()
+    assert items <= resident
+    b.step(16)  # one persistent launch
+    torch.cuda.synchronize()
+    for name, a, s in zip(FAMILY_SHAPES, alone, sols):
+        assert s.step_count == 40
+        assert np.array_equal(s.get_dist(), a), name
+    assert all(d["status"] == 0 for d in b.diag())
+    b.close()
+
+
 def test_batch_matches_oracle_fp32():
     from paper_1806_10241_gb300.batch import Batch
     from paper_1806_10241_gb300.solver import Solver
