@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-FIELDS = ("nu_i", "nu_o", "nu_avg", "mass", "mass_r", "T_sum", "u_max")
+FIELDS = ("nu_i", "nu_o", "nu_avg", "mass", "mass_r", "T_sum", "u_max", "k_eq_i", "k_eq_o")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -46,7 +46,7 @@ def _static_diag(solver, step):
     _abi.check(st)
     return {"nu_side": list(out.nu_side), "nu_i": out.nu_i, "nu_o": out.nu_o, "nu_avg": out.nu_avg,
             "mass": out.mass, "mass_r": out.mass_r, "T_sum": out.T_sum, "u_max": out.u_max,
-            "step": int(out.step), "status": int(out.status)}
+            "k_eq_i": out.k_eq_i, "k_eq_o": out.k_eq_o, "step": int(out.step), "status": int(out.status)}
 
 
 def _cases():
@@ -54,7 +54,10 @@ def _cases():
     return [("cylinder_fp32", W.swirling_cylinder(nr=70, nz=96, Re=200.0, Ra=1e4, amp=1e-3, seed=2), "fp32"),
             ("annulus_fp64", W.annulus_convection(nr=33, nz=40, Ra=1e4, amp=1e-3, seed=4, swirl_inner=0.01),
              "fp64"),
-            ("annulus_fp16", W.annulus_convection(nr=61, nz=45, Ra=1e4, amp=1e-3, seed=5), "fp16")]
+            ("annulus_fp16", W.annulus_convection(nr=61, nz=45, Ra=1e4, amp=1e-3, seed=5), "fp16"),
+            # the top split into a crystal and a free surface with the ramp: Nu over heated segments
+            ("czochralski_fp32", W.czochralski(nr=60, nz=60, beta=0.4, Re_x=200.0, Re_c=-50.0, Pr=0.7, Gr=1e4),
+             "fp32")]
 
 
 @pytest.mark.parametrize("name,case,storage", _cases(), ids=lambda x: x if isinstance(x, str) else "")
