@@ -409,8 +409,7 @@ def _ulp16(x, mant_bits):
 
 
 @pytest.mark.parametrize("storage,mant,scale", [("fp16", 10, 1024.0), ("bf16", 7, 1.0)])
-@pytest.mark.parametrize("name", ["annulus_walls", "cylinder_axis", "periodic_annulus", "czochralski",
-                                  "free_ends_annulus"])
+@pytest.mark.parametrize("name", list(BUILDERS))
 def test_16bit_distributions_after_one_step_within_one_rounding(name, storage, mant, scale):
     """One step from a state the 16-bit buffer holds exactly: every stored
     value equals the oracle's to within one stochastic rounding of its
