@@ -67,9 +67,10 @@ def kernel_name(storage, row_fetch):
     return {1: "k_step2", 2: "k_step2_tma", 3: "k_step3_tma"}[row_fetch]
 
 
-def counters_for(key):
-    """Per-launch DRAM traffic from the committed ncu summary, only while the
-    kernel source still matches the one the counters were taken on."""
+def counters_for(key, what="dram_bytes_per_launch"):
+    """A per-launch counter (DRAM traffic, warp instructions) from the
+    committed ncu summary, only while the kernel source and build flags still
+    match the ones the counters were taken on."""
     try:
         with open(PROFILE_JSON) as f:
             d = json.load(f)
@@ -78,7 +79,24 @@ def counters_for(key):
     e = d.get(key)
     if not e or e.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    return e.get(what)
+
+
+def issue_roofline(key, ms_per_step, sm_mhz):
+    """Warp instructions per launch (ncu smsp__inst_executed.sum, committed)
+    against the issue ceiling: every SM's four schedulers issue at most one
+    warp instruction per cycle, at the SM clock seen under load."""
+    import torch
+    inst = counters_for(key, "warp_instructions_per_launch")
+    if inst is None or not sm_mhz:
+        return None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    achieved = inst / (ms_per_step * 1e-3) / 1e9
+    peak = sms * 4 * sm_mhz * 1e6 / 1e9
+    return {"bound": "issue", "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "G warp-instructions/s", "frac": round(achieved / peak, 4),
+            "warp_instructions_per_launch": inst,
+            "peak_kind": f"{sms} SMs x 4 schedulers x 1 warp instruction per cycle x {sm_mhz:.0f} MHz"}
 
 
 # ---- clocks -------------------------------------------------------------------
@@ -452,7 +470,7 @@ def run_reference(args):
     return 0
 
 
-def storage_forms(case, steps, warmup, repeats):
+def storage_forms(case, steps, warmup, repeats, sm_mhz=None):
     """The benchmark lattice in FP32, FP16 and BF16 storage, each from the
     same initial state: `warmup` steps, then `repeats` timed regions of
     `steps` steps (median); Nu of the 16-bit forms against the FP32 run after
@@ -483,6 +501,10 @@ def storage_forms(case, steps, warmup, repeats):
                         "roofline_frac": round(bpn * nodes / (med / steps * 1e-3) / 1e9 / peak, 4),
                         "algorithmic_bytes_per_node": bpn, "nu_avg": d["nu_avg"],
                         "steps_total": warmup + steps * repeats, "status": d["status"]}
+        kname = kernel_name(storage, g.get_launch()[2])
+        iss = issue_roofline(f"{kname}_{storage}_{case.nr}x{case.nz}", med / steps, sm_mhz)
+        if iss is not None:
+            out[storage]["issue"] = iss
         del g
         torch.cuda.empty_cache()
     for storage in ("fp16", "bf16"):
@@ -492,12 +514,12 @@ def storage_forms(case, steps, warmup, repeats):
     return out
 
 
-def extras(case, args):
+def extras(case, args, sm_mhz=None):
     """Sub-results measured in the same run, a few seconds each: the 16-bit
     storage forms of the benchmark lattice, the 256-lattice batch and a short
     serving stream."""
     res = {}
-    forms = storage_forms(case, steps=500, warmup=50, repeats=10)
+    forms = storage_forms(case, steps=500, warmup=50, repeats=10, sm_mhz=sm_mhz)
     res["fp16"] = forms["fp16"]
     res["bf16"] = forms["bf16"]
     res["fp16"]["fp32_same_schedule"] = {k: forms["fp32"][k] for k in ("value", "ms_per_step", "nu_avg")}
@@ -675,6 +697,8 @@ def main():
                 "algorithmic_bytes_per_node": bpn,
                 "kernel": f"{kname} (fused stream + sources + collisions + boundaries, one launch per step)"}
 
+    clk = clocks.summary(t0, t1)
+    iss = issue_roofline(key, ms_per_step, clk.get("sm_mhz"))
     line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -688,12 +712,14 @@ def main():
                         "mlups_min": round(job_mlups(world, nodes, args.steps, ms_sorted[-1]), 1),
                         "mlups_max": round(job_mlups(world, nodes, args.steps, ms_sorted[0]), 1)},
             "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps * len(ms_all),
-            "clocks": clocks.summary(t0, t1),
+            "clocks": clk,
             "diag": {"nu_avg": d["nu_avg"], "mass": d["mass"], "status": d["status"]}}
+    if iss is not None:
+        line["issue_roofline"] = iss  # the same kernel against the schedulers' issue ceiling, for context
     del g
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_extras:
-        line.update(extras(case, args))
+        line.update(extras(case, args, clk.get("sm_mhz")))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_mlups(case.nr, case.nz, args.cpu_budget)
     if rank == 0:

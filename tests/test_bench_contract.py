@@ -49,6 +49,9 @@ def test_gpu_arm_line():
     e = line["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert "sm_mhz" in line["clocks"] and line["diag"]["status"] == 0
+    if "issue_roofline" in line:  # present while the committed instruction count matches the build
+        i = line["issue_roofline"]
+        assert i["bound"] == "issue" and 0.0 < i["frac"] < 1.0 and abs(i["frac"] - i["achieved"] / i["peak"]) < 1e-3
 
 
 @pytest.mark.gpu
