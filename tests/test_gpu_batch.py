@@ -277,6 +277,38 @@ def test_persistent_batch_equals_launch_per_step(storage):
         assert np.array_equal(a, p), c.name
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_persistent_batch_over_every_boundary_family_for_1000_steps(storage):
+    """Row fetch 5 over lattices of every boundary family, 1000 steps in
+    calls of uneven length (each a persistent launch whose items wait on
+    their neighbours' progress), against one launch per step: the same bits."""
+    from test_gpu_parity import BUILDERS, random_state
+    from paper_1806_10241_gb300 import _abi
+    from paper_1806_10241_gb300.batch import Batch
+    from paper_1806_10241_gb300.solver import Solver
+    params = [BUILDERS[name](*shape) for name, shape in FAMILY_SHAPES.items()]
+    states = [random_state(p, seed) for seed, p in enumerate(params)]
+    runs = []
+    for fetch, seg, graph, call in ((3, 4, 10, 500), (5, 3, 0, 97)):
+        stream = torch.cuda.Stream()
+        sols = []
+        for p, st in zip(params, states):
+            s = Solver(p, storage=storage, stream=stream)
+            s.set_dist(st)
+            sols.append(s)
+        b = Batch(sols, stream=stream, seg_rows=seg, warps_per_block=2, graph_steps=graph, row_fetch=fetch)
+        left = 1000
+        while left > 0:
+            b.step(min(left, call))
+            left -= call
+        torch.cuda.synchronize()
+        assert all(d["status"] != _abi.LB_ERR_TIMEOUT for d in b.diag())  # no wait ran out
+        runs.append([s.get_dist() for s in sols])
+        b.close()
+    for name, a, p in zip(FAMILY_SHAPES, runs[0], runs[1]):
+        assert np.array_equal(a, p), name
+
+
 def test_persistent_batch_rejects_more_items_than_resident_warps():
     from paper_1806_10241_gb300._abi import LBError
     from paper_1806_10241_gb300.batch import Batch
