@@ -227,6 +227,39 @@ def test_batch_diagnostics_follow_a_changed_launch():
     b.close()
 
 
+def test_batch_orders_work_queued_on_the_lattices_own_streams():
+    """Each lattice on a stream of its own, the batch on another: work queued
+    on a lattice's stream (initial fields, a state upload) runs before the
+    batch's next step, and the batch's steps before the lattice's next
+    download, without any synchronisation by the caller."""
+    from paper_1806_10241_gb300.batch import Batch
+    from paper_1806_10241_gb300.solver import Solver
+    cases = _cases()[:5]
+    ref = []
+    for c in cases:
+        s = Solver(c.params, storage="fp32")
+        s.init_fields(c.fields)
+        s.step(30)
+        if c is cases[2]:
+            s.set_dist(s.get_dist() * 1.0001)
+        s.step(20)
+        ref.append(s.get_dist())
+        s.close()
+    sols = []
+    for c in cases:
+        s = Solver(c.params, storage="fp32", stream=torch.cuda.Stream())
+        s.init_fields(c.fields)  # queued on the lattice's stream
+        sols.append(s)
+    b = Batch(sols, stream=torch.cuda.Stream(), graph_steps=10)
+    b.step(30)
+    mid = sols[2].get_dist()  # on the lattice's stream, after the batch's steps
+    sols[2].set_dist(mid * 1.0001)
+    b.step(20)
+    for c, s, want in zip(cases, sols, ref):
+        assert np.array_equal(s.get_dist(), want), c.name
+    b.close()
+
+
 def test_segment_plan_rejects_out_of_range_values():
     from paper_1806_10241_gb300._abi import LBError
     from paper_1806_10241_gb300.batch import Batch
