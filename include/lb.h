@@ -216,7 +216,11 @@ LB_EXPORT lb_status lb_selftest_timeout(lb_ctx *ctx, int32_t polls);
 LB_EXPORT lb_status lb_stream_function(lb_ctx *ctx, double *host_psi, double *psi_max);
 
 /* Distributions as absolute values, host [19][nz][nr] doubles: f0..f8,
- * g0..g4, h0..h4 (velocity order of Eq. 10 and Eq. 28).  Synchronous. */
+ * g0..g4, h0..h4 (velocity order of Eq. 10 and Eq. 28).  Synchronous.
+ * The rest-state offset is added (get) and subtracted (set) in FP64, so a
+ * get followed by a set can move a stored deviation smaller than about
+ * 1e-9 by one unit of the storage type; lb_get_state / lb_set_state restore
+ * a state bitwise. */
 LB_EXPORT lb_status lb_get_distributions(lb_ctx *ctx, double *host19);
 LB_EXPORT lb_status lb_set_distributions(lb_ctx *ctx, const double *host19);
 
