@@ -218,9 +218,10 @@ LB_EXPORT lb_status lb_stream_function(lb_ctx *ctx, double *host_psi, double *ps
 /* Distributions as absolute values, host [19][nz][nr] doubles: f0..f8,
  * g0..g4, h0..h4 (velocity order of Eq. 10 and Eq. 28).  Synchronous.
  * The rest-state offset is added (get) and subtracted (set) in FP64, so a
- * get followed by a set can move a stored deviation smaller than about
- * 1e-9 by one unit of the storage type; lb_get_state / lb_set_state restore
- * a state bitwise. */
+ * get followed by a set can move a stored deviation by up to half an FP64
+ * unit of the rest value (about 3e-17): in FP64 storage any deviation, in
+ * FP32 storage only those below about 1e-9 (by one FP32 unit).
+ * lb_get_state / lb_set_state restore a state bitwise. */
 LB_EXPORT lb_status lb_get_distributions(lb_ctx *ctx, double *host19);
 LB_EXPORT lb_status lb_set_distributions(lb_ctx *ctx, const double *host19);
 
