@@ -203,6 +203,45 @@ def test_fp32_fields_after_1000_steps(case):
     assert dg["T_sum"] == pytest.approx(do["T_sum"], rel=1e-6)
 
 
+def smooth_fields(params, seed):
+    """Rest, a stratified temperature and a small seeded perturbation: the
+    walls drive the flow from there."""
+    rng = np.random.default_rng(seed)
+    nz, nr = params["nz"], params["nr"]
+    f = np.zeros((5, nz, nr))
+    f[0] = 1.0
+    zz = (np.arange(nz)[:, None] + 0.5) / nz
+    f[4] = params.get("T0", 0.5) + 0.2 * (0.5 - zz) + 1e-3 * rng.uniform(-1, 1, (nz, nr))
+    return f
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-5), ("fp64", 1e-10)])
+@pytest.mark.parametrize("name", list(BUILDERS))
+def test_fields_after_1000_steps_every_family(name, storage, tol):
+    """Every boundary family run 1000 steps from the same smooth state on the
+    GPU and in the oracle: velocity and temperature within relative L2 tol
+    (a component that vanishes in the exact flow, like u_r of axial Couette
+    flow, is measured against the velocity's norm), Nu within 1e-4 (FP32)."""
+    params = BUILDERS[name](48, 40)
+    fl = smooth_fields(params, 3)
+    o = oracle.Oracle(params)
+    o.init_fields(fl)
+    o.step(1000)
+    want, do = o.fields(), o.diag()
+    g = Solver(params, storage=storage)
+    g.init_fields(fl)
+    g.step(1000)
+    got, dg = g.fields(), g.diag()
+    assert dg["status"] == 0
+    vel = np.linalg.norm(want[1:4])
+    for q in (1, 2, 3):
+        err = np.linalg.norm(got[q] - want[q]) / max(np.linalg.norm(want[q]), vel)
+        assert err < tol, (name, q, err)
+    assert _rel_l2(got[4], want[4]) < tol, (name, "T")
+    if do["nu_avg"] != 0.0:
+        assert dg["nu_avg"] == pytest.approx(do["nu_avg"], rel=1e-4 if storage == "fp32" else 1e-10)
+
+
 @pytest.mark.parametrize("name", ["annulus_walls", "cylinder_axis", "periodic_annulus", "czochralski",
                                   "free_ends_annulus"])
 def test_fp64_fields_and_diagnostics_match_oracle(name):
