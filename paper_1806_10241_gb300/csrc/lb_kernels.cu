@@ -848,11 +848,9 @@ template <typename S> constexpr int kRingStages = 4;
 // march3 forms, as measured on GB300 (all give the same bits): the
 // single-lattice FP32 step takes the separate interior form of the row update
 // (+5 %; in 16-bit storage it cost 2-3 %) and every kernel reads the wall and
-// axis values from the ring, except the batched FP32 step, whose warps on
-// small lattices nearly all hold a wall or the axis and ran 6 % faster with
-// the values from global memory.
+// axis values from the ring (the batched FP32 step on serving-size lattices,
+// where nearly every warp holds a wall or the axis: +10 % over global loads).
 template <typename S> constexpr bool kStepSplit = sizeof(S) == 4;
-template <typename S> constexpr bool kBatchOwnStage = sizeof(S) != 4;
 
 template <typename S>
 __host__ __device__ size_t ring_smem_bytes(int wpb)
@@ -1409,7 +1407,7 @@ __global__ void __maxnreg__(LB_STEP3_MAXREG) k_batch3(const BatchDesc *__restric
         rs.lane = lane;
         rs.status = bd->status;
         rs.start();
-        march3<S, R, false, kBatchOwnStage<S>>(k, (const S *)bd->buf[cur], (S *)bd->buf[cur ^ 1], w * 64, s, e,
+        march3<S, R, false, true>(k, (const S *)bd->buf[cur], (S *)bd->buf[cur ^ 1], w * 64, s, e,
                                                salt_of(bd->step0 + t), rs);
     }
 }
