@@ -95,6 +95,14 @@ template <typename C> struct KP {
     C ramp0, ramp1;       // wall temperature ramp of entry 4: T_w(y) = ramp0 + ramp1 y
     C scale, inv_scale;
     C r0c, roc;           // inner and outer wall radii, rounded once
+    // Lateral walls (sides 2 and 3), computed once in the kernel's precision
+    // with the operations the per-row rules would do (pair kernels): latf, the
+    // moving-wall terms of the populations entering from the wall (f2, f5, f6
+    // at the inner side, f4, f7, f8 at the outer); (latgs, latgc) and
+    // (laths, lathc), the sign and constant of the scalar rule of g and h,
+    // x = s x_own + c; (gha, ghb), the ghost values a q + b of u_x, u_y,
+    // u_theta and T for the central differences.
+    C latf[2][3], latgs[2], latgc[2], laths[2], lathc[2], gha[2][4], ghb[2][4];
     const float *ytab;    // y[pitch] then 1/y[pitch] (pair kernels)
     // Nusselt and equivalent-conductivity scales per side (diagnostics)
     double nu_scale[4], keq_scale[4];
@@ -145,6 +153,36 @@ template <typename C> KP<C> make_kp(const HostParams &h)
     k.inv_scale = (C)(1.0 / h.scale);
     k.r0c = (C)h.r0;
     k.roc = (C)(h.r0 + h.nr);
+    for (int j = 0; j < 2; ++j) {
+        const int sd = 2 + j;
+        const C rw = k.rho0, ux = k.uwx[sd], uy = k.uwy[sd], radius = j == 0 ? k.r0c : k.roc;
+        const C c9 = (C)(6.0 / 9.0), c36 = (C)(6.0 / 36.0), two = (C)2;
+        if (j == 0) {  // Sec. 3.1 moving wall (R11) at the inner side
+            k.latf[0][0] = rw * c9 * uy;
+            k.latf[0][1] = rw * c36 * (ux + uy);
+            k.latf[0][2] = rw * c36 * (-ux + uy);
+        } else {
+            k.latf[1][0] = rw * c9 * (-uy);
+            k.latf[1][1] = rw * c36 * (-ux - uy);
+            k.latf[1][2] = rw * c36 * (ux - uy);
+        }
+        // scalar rules (R12, R13): Dirichlet -x + (2/6) w, odd axis -x, else x
+        const C psi_w = k.rho0 * k.omega[sd] * radius, t_w = k.Tw[sd] - k.T0;
+        k.latgs[j] = (C)(k.swirl[sd] == 0 || k.swirl[sd] == 2 ? -1 : 1);
+        k.latgc[j] = k.swirl[sd] == 0 ? (C)(2.0 / 6.0) * psi_w : (C)0;
+        k.laths[j] = (C)(k.heat[sd] == 0 ? -1 : 1);
+        k.lathc[j] = k.heat[sd] == 0 ? (C)(2.0 / 6.0) * t_w : (C)0;
+        // ghosts (R7): wall 2 q_w - q, zero flux q, axis u_x, T even, u_y, u_theta odd
+        const bool axis = k.flow[sd] == 1;
+        k.gha[j][0] = (C)(axis ? 1 : -1);
+        k.ghb[j][0] = axis ? (C)0 : two * ux;
+        k.gha[j][1] = (C)-1;
+        k.ghb[j][1] = axis ? (C)0 : two * uy;
+        k.gha[j][2] = (C)(k.swirl[sd] == 0 || k.swirl[sd] == 2 ? -1 : 1);
+        k.ghb[j][2] = k.swirl[sd] == 0 ? two * k.omega[sd] * radius : (C)0;
+        k.gha[j][3] = (C)(k.heat[sd] == 0 ? -1 : 1);
+        k.ghb[j][3] = k.heat[sd] == 0 ? two * k.Tw[sd] : (C)0;
+    }
     k.ytab = h.ytab;
     // Nusselt normalisation (Sec. 3.2): lateral walls -R_w / (H dT), end
     // walls -(H / dT) * 2 / (R_o^2 - R_i^2); dT from the Dirichlet values.

@@ -684,46 +684,38 @@ __device__ __forceinline__ void row_tail(const KP<float> &k, const Own &own, S *
     const float sc = k.scale;
     // lateral boundaries: column 0 is always the x of a pair, column
     // nr - 1 the x or the y
+    // (the wall terms and rule coefficients come precomputed in k.latf,
+    // k.latgs / latgc, k.laths / lathc: one add or one FMA per value)
     if (edge_warp) {
-        const float rw = k.rho0;
         if (atA0) {
-            const int sd = 2;
-            if (k.flow[sd] == 1) {  // axis: mirror images
+            if (k.flow[2] == 1) {  // axis: mirror images
                 fv[2].v.x = own.own0(4);
                 if (has_m) fv[5].v.x = own.m8();
                 if (has_p) fv[6].v.x = own.p7();
             } else {
-                const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
-                fv[2].v.x = own.own0(4) + rw * (6.0f / 9.0f) * uy_w;
-                fv[5].v.x = own.own0(7) + rw * (6.0f / 36.0f) * (ux_w + uy_w);
-                fv[6].v.x = own.own0(8) + rw * (6.0f / 36.0f) * (-ux_w + uy_w);
+                fv[2].v.x = own.own0(4) + k.latf[0][0];
+                fv[5].v.x = own.own0(7) + k.latf[0][1];
+                fv[6].v.x = own.own0(8) + k.latf[0][2];
             }
-            gv[2].v.x = scalar_bc<float>(k.swirl[sd], own.own0(G0 + 4),
-                                         wall_psi<float>(k, sd, y2.v.x), true);
-            hv5[2].v.x = scalar_bc<float>(k.heat[sd], own.own0(H0 + 4), k.Tw[sd] - k.T0, false);
+            gv[2].v.x = __fmaf_rn(k.latgs[0], own.own0(G0 + 4), k.latgc[0]);
+            hv5[2].v.x = __fmaf_rn(k.laths[0], own.own0(H0 + 4), k.lathc[0]);
         }
         if (atAN || atBN) {
-            const int sd = 3;
-            const float ux_w = k.uwx[sd], uy_w = k.uwy[sd];
             const F2 o2 = own.own(2), o5 = own.own(5), o6 = own.own(6);
             const F2 og = own.own(G0 + 2), oh = own.own(H0 + 2);
-            const float a4 = k.rho0 * (6.0f / 9.0f) * (-uy_w);
-            const float a7 = k.rho0 * (6.0f / 36.0f) * (-ux_w - uy_w);
-            const float a8 = k.rho0 * (6.0f / 36.0f) * (ux_w - uy_w);
-            const float psw = wall_psi<float>(k, sd, 0.0f), tw = k.Tw[sd] - k.T0;
             if (atAN) {
-                fv[4].v.x = o2.v.x + a4;
-                fv[7].v.x = o5.v.x + a7;
-                fv[8].v.x = o6.v.x + a8;
-                gv[4].v.x = scalar_bc<float>(k.swirl[sd], og.v.x, psw, true);
-                hv5[4].v.x = scalar_bc<float>(k.heat[sd], oh.v.x, tw, false);
+                fv[4].v.x = o2.v.x + k.latf[1][0];
+                fv[7].v.x = o5.v.x + k.latf[1][1];
+                fv[8].v.x = o6.v.x + k.latf[1][2];
+                gv[4].v.x = __fmaf_rn(k.latgs[1], og.v.x, k.latgc[1]);
+                hv5[4].v.x = __fmaf_rn(k.laths[1], oh.v.x, k.lathc[1]);
             }
             if (atBN) {
-                fv[4].v.y = o2.v.y + a4;
-                fv[7].v.y = o5.v.y + a7;
-                fv[8].v.y = o6.v.y + a8;
-                gv[4].v.y = scalar_bc<float>(k.swirl[sd], og.v.y, psw, true);
-                hv5[4].v.y = scalar_bc<float>(k.heat[sd], oh.v.y, tw, false);
+                fv[4].v.y = o2.v.y + k.latf[1][0];
+                fv[7].v.y = o5.v.y + k.latf[1][1];
+                fv[8].v.y = o6.v.y + k.latf[1][2];
+                gv[4].v.y = __fmaf_rn(k.latgs[1], og.v.y, k.latgc[1]);
+                hv5[4].v.y = __fmaf_rn(k.laths[1], oh.v.y, k.lathc[1]);
             }
         }
     }
@@ -841,39 +833,25 @@ __device__ __forceinline__ void row_tail(const KP<float> &k, const Own &own, S *
     F2 Lut = mk2(lut, pm_cur.ut.v.x), LT = mk2(lT, pm_cur.T.v.x);
     F2 Rux = mk2(pm_cur.ux.v.y, rux), Ruy = mk2(pm_cur.uy.v.y, ruy);
     F2 Rut = mk2(pm_cur.ut.v.y, rut), RT = mk2(pm_cur.T.v.y, rT);
+    // ghosts at the lateral walls, a q + b (k.gha, k.ghb)
     if (edge_warp) {
         if (atA0) {
-            const int sd = 2;
-            const float ux = pm_cur.ux.v.x, uy = pm_cur.uy.v.x, ut = pm_cur.ut.v.x, T = pm_cur.T.v.x;
-            if (k.flow[sd] == 1) {
-                Lux.v.x = ux;
-                Luy.v.x = -uy;
-            } else {
-                Lux.v.x = 2.0f * k.uwx[sd] - ux;
-                Luy.v.x = 2.0f * k.uwy[sd] - uy;
-            }
-            const int sw = k.swirl[sd], ht = k.heat[sd];
-            Lut.v.x = sw == 2 ? -ut : (sw == 0 ? 2.0f * k.omega[sd] * k.r0c - ut : ut);
-            LT.v.x = ht == 0 ? 2.0f * k.Tw[sd] - T : T;
+            Lux.v.x = __fmaf_rn(k.gha[0][0], pm_cur.ux.v.x, k.ghb[0][0]);
+            Luy.v.x = __fmaf_rn(k.gha[0][1], pm_cur.uy.v.x, k.ghb[0][1]);
+            Lut.v.x = __fmaf_rn(k.gha[0][2], pm_cur.ut.v.x, k.ghb[0][2]);
+            LT.v.x = __fmaf_rn(k.gha[0][3], pm_cur.T.v.x, k.ghb[0][3]);
         }
-        if (atAN || atBN) {
-            const int sd = 3;
-            const int sw = k.swirl[sd], ht = k.heat[sd];
-            const float Ro = k.roc;
-            if (atAN) {
-                const float ux = pm_cur.ux.v.x, uy = pm_cur.uy.v.x, ut = pm_cur.ut.v.x, T = pm_cur.T.v.x;
-                Rux.v.x = 2.0f * k.uwx[sd] - ux;
-                Ruy.v.x = 2.0f * k.uwy[sd] - uy;
-                Rut.v.x = sw == 0 ? 2.0f * k.omega[sd] * Ro - ut : ut;
-                RT.v.x = ht == 0 ? 2.0f * k.Tw[sd] - T : T;
-            }
-            if (atBN) {
-                const float ux = pm_cur.ux.v.y, uy = pm_cur.uy.v.y, ut = pm_cur.ut.v.y, T = pm_cur.T.v.y;
-                Rux.v.y = 2.0f * k.uwx[sd] - ux;
-                Ruy.v.y = 2.0f * k.uwy[sd] - uy;
-                Rut.v.y = sw == 0 ? 2.0f * k.omega[sd] * Ro - ut : ut;
-                RT.v.y = ht == 0 ? 2.0f * k.Tw[sd] - T : T;
-            }
+        if (atAN) {
+            Rux.v.x = __fmaf_rn(k.gha[1][0], pm_cur.ux.v.x, k.ghb[1][0]);
+            Ruy.v.x = __fmaf_rn(k.gha[1][1], pm_cur.uy.v.x, k.ghb[1][1]);
+            Rut.v.x = __fmaf_rn(k.gha[1][2], pm_cur.ut.v.x, k.ghb[1][2]);
+            RT.v.x = __fmaf_rn(k.gha[1][3], pm_cur.T.v.x, k.ghb[1][3]);
+        }
+        if (atBN) {
+            Rux.v.y = __fmaf_rn(k.gha[1][0], pm_cur.ux.v.y, k.ghb[1][0]);
+            Ruy.v.y = __fmaf_rn(k.gha[1][1], pm_cur.uy.v.y, k.ghb[1][1]);
+            Rut.v.y = __fmaf_rn(k.gha[1][2], pm_cur.ut.v.y, k.ghb[1][2]);
+            RT.v.y = __fmaf_rn(k.gha[1][3], pm_cur.T.v.y, k.ghb[1][3]);
         }
     }
     const F2 hf = sp(0.5f);

@@ -25,7 +25,9 @@ def _stream(n=7):
         c = W.annulus_convection(nr=nr, nz=nr + 8 * (i % 3), Ra=10 ** (3 + (i % 3) * 0.5), amp=1e-4, seed=i,
                                  swirl_inner=0.01 * (i % 2))
         c.name = f"r{i}"
-        out.append(W.Request(i, 0.02 * i, c))
+        # half of the stream at once (so that requests share the device however
+        # fast each one finishes), the rest arriving while those run
+        out.append(W.Request(i, 0.0 if i % 2 == 0 else 0.003 * i, c))
     return out
 
 
