@@ -210,7 +210,7 @@ def oracle_mlups(nr, nz_full, budget_s, max_rows=None):
 
 def serving_measure(requests, nr_lo, nr_hi, max_steps, storage, node_budget=0):
     """A Poisson stream of solve requests (rate 50/s, seed 0) served by the
-    continuous-batching server (autotuned batched launches, graphs of 10) and,
+    continuous-batching server (autotuned batched launches, graphs of 50) and,
     for comparison, by sequential plain FP32 solves; both with the steady
     test |dNu| < 1e-6 over 1000 steps and the step cap max_steps."""
     import torch
@@ -218,7 +218,7 @@ def serving_measure(requests, nr_lo, nr_hi, max_steps, storage, node_budget=0):
     from paper_1806_10241_gb300.serving import Server
     reqs = W.serving_requests(count=requests, rate=50.0, seed=0, nr_lo=nr_lo, nr_hi=nr_hi)
     kw = dict(steps_per_round=500, check_every=500, window=1000, tol=1e-6, max_steps=max_steps)
-    srv = Server(storage=storage, graph_steps=10, autotune=True, node_budget=node_budget or None, **kw)
+    srv = Server(storage=storage, graph_steps=50, autotune=True, node_budget=node_budget or None, **kw)
     rep_b = srv.run(reqs)
     rep_s = Server(storage=storage, **kw).run_sequential(reqs, storage="fp32")
     torch.cuda.synchronize()
@@ -524,7 +524,7 @@ def extras(case, args, sm_mhz=None):
     res["bf16"] = forms["bf16"]
     res["fp16"]["fp32_same_schedule"] = {k: forms["fp32"][k] for k in ("value", "ms_per_step", "nu_avg")}
     res["bf16"]["fp32_same_schedule"] = res["fp16"]["fp32_same_schedule"]
-    b = batch_measure(256, 32, 512, "fp16", steps=100, warmup=20, graph_steps=10, oracle_instances=3, repeats=5)
+    b = batch_measure(256, 32, 512, "fp16", steps=100, warmup=20, graph_steps=50, oracle_instances=3, repeats=5)
     res["batch"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "mlups_range", "config", "nu_vs_oracle")}
     res["batch"]["roofline_frac"] = b["roofline"]["frac"]
     sv = serving_measure(args.serve_requests, 64, 96, args.serve_max_steps, "fp32")
@@ -566,7 +566,7 @@ def main():
     ap.add_argument("--batch-storage", dest="batch_storage", default="fp16", choices=["fp16", "bf16", "fp32"])
     ap.add_argument("--batch-lo", dest="batch_lo", type=int, default=32)
     ap.add_argument("--batch-hi", dest="batch_hi", type=int, default=512)
-    ap.add_argument("--graph-steps", dest="graph_steps", type=int, default=10)
+    ap.add_argument("--graph-steps", dest="graph_steps", type=int, default=50)
     ap.add_argument("--oracle-instances", dest="oracle_instances", type=int, default=3)
     ap.add_argument("--prec-steps", dest="prec_steps", type=int, default=2000)
     ap.add_argument("--prec-oracle-steps", dest="prec_oracle_steps", type=int, default=1500)

@@ -109,7 +109,7 @@ def _apply(batch, launch, waves, graph_steps):
         batch.set_segments(None)
 
 
-def tune_batch(batch, steps: int = 10, graph_steps: int = 10, use_cache: bool = True) -> tuple:
+def tune_batch(batch, steps: int = 30, graph_steps: int = 50, use_cache: bool = True) -> tuple:
     """Pick the batch's launch: (seg_rows, warps_per_block, row_fetch) for
     every lattice, or a per-lattice segment plan (segment_plan) for a number
     of waves, with the TMA-ring step; keyed by storage, node count and

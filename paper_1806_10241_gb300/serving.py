@@ -99,7 +99,7 @@ class Server:
     def __init__(self, storage: str = "fp16", steps_per_round: int = 500, check_every: int = 500,
                  window: int = 1000, tol: float = 1e-6, max_steps: int = 200_000,
                  hbm_budget: int | None = None, reserve_bytes: int = 1 << 30, max_active: int = 512,
-                 graph_steps: int = 10, seg_rows: int = 0, warps_per_block: int = 0,
+                 graph_steps: int = 50, seg_rows: int = 0, warps_per_block: int = 0,
                  device: str = "cuda", keep_results: bool = False, autotune: bool = False,
                  node_budget: int | None = None):
         if check_every % steps_per_round:
