@@ -109,13 +109,29 @@ def _apply(batch, launch, waves, graph_steps):
         batch.set_segments(None)
 
 
+def _batch_key(batch) -> str:
+    return f"batch/{batch.solvers[0].storage}/{_size_class(batch.nodes)}/{_size_class(len(batch.solvers))}"
+
+
+def has_cached_batch_launch(batch, graph_steps: int = 50) -> bool:
+    """Whether tune_batch would take this batch's launch from the cache (and
+    so take no steps); applies that launch when it does."""
+    with _lock:
+        e = _load().get(_batch_key(batch))
+    if not e or len(e.get("launch", [])) != 3 or "waves" not in e:
+        return False
+    _apply(batch, tuple(e["launch"]), e["waves"], graph_steps)
+    resident, items = batch.occupancy()
+    return e["launch"][2] != 5 or items <= resident
+
+
 def tune_batch(batch, steps: int = 30, graph_steps: int = 50, use_cache: bool = True) -> tuple:
     """Pick the batch's launch: (seg_rows, warps_per_block, row_fetch) for
     every lattice, or a per-lattice segment plan (segment_plan) for a number
     of waves, with the TMA-ring step; keyed by storage, node count and
     lattice count.  Returns (seg_rows, warps_per_block, row_fetch, waves),
     waves = 0 for a common segment length."""
-    key = f"batch/{batch.solvers[0].storage}/{_size_class(batch.nodes)}/{_size_class(len(batch.solvers))}"
+    key = _batch_key(batch)
     with _lock:
         cache = _load() if use_cache else {}
     if key in cache and len(cache[key].get("launch", [])) == 3 and "waves" in cache[key]:

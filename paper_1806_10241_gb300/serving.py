@@ -29,7 +29,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from .autotune import tune_batch
+from .autotune import has_cached_batch_launch, tune_batch
 from .batch import Batch
 from .solver import Solver, required_bytes
 from .workloads import Request
@@ -137,6 +137,28 @@ class Server:
         rec.admitted = now
         return _Active(req, s, rec, required_bytes(req.case.params, self.storage))
 
+    def _tune(self, batch: Batch, active: list, used: int) -> None:
+        """The batch's launch from the autotuner (cached per storage and size
+        class).  On a cache miss the candidates are timed on scratch copies
+        of the active lattices, so that the live ones take no extra steps:
+        their steady-state checks then fall on the same steps as in a solo
+        run, and so do the results.  Only when the copies would not fit the
+        memory budget are the live lattices tuned (the tuning steps are
+        real steps)."""
+        if not has_cached_batch_launch(batch, self.graph_steps) and 2 * used <= self.budget:
+            scratch = []
+            for a in active:
+                s = Solver(a.req.case.params, storage=self.storage, device=self.device, stream=self.stream)
+                s.init_fields(a.req.case.fields)
+                scratch.append(s)
+            sb = Batch(scratch, stream=self.stream, seg_rows=self.seg_rows, warps_per_block=self.warps_per_block,
+                       graph_steps=self.graph_steps)
+            tune_batch(sb, steps=3, graph_steps=self.graph_steps)
+            sb.close()
+            for s in scratch:
+                s.close()
+        tune_batch(batch, steps=3, graph_steps=self.graph_steps)
+
     def _check(self, a: _Active, d: dict | None = None) -> bool:
         """Diagnostics of an active lattice (given, or computed here); True
         when it is finished."""
@@ -209,8 +231,8 @@ class Server:
                     batch.close()
                 batch = Batch([a.solver for a in active], stream=self.stream, seg_rows=self.seg_rows,
                               warps_per_block=self.warps_per_block, graph_steps=self.graph_steps)
-                if self.autotune:  # cached per storage and size class; tuning steps are real steps
-                    tune_batch(batch, steps=3, graph_steps=self.graph_steps)
+                if self.autotune:
+                    self._tune(batch, active, used)
                 dirty = False
             batch.step(self.steps_per_round)
             rounds += 1

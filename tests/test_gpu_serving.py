@@ -172,3 +172,25 @@ def test_node_budget_limits_the_lattices_stepped_together():
     assert [r.rid for r in admitted] == sorted(r.rid for r in rep.records)  # arrival order
     for r in rep.records:
         assert np.array_equal(srv.results[r.rid], _alone(reqs[r.rid], r.steps, "fp32", 100)), r.name
+
+
+def test_autotuned_server_stops_every_request_where_a_solo_run_does(tmp_path, monkeypatch):
+    """With an empty autotuner cache the server times the launch candidates on
+    scratch copies of the active lattices, so the live ones take no extra
+    steps: every request is checked at the same steps as in a sequential solo
+    run, reaches the same verdict at the same step, and ends in the same bits."""
+    from paper_1806_10241_gb300 import autotune
+    from paper_1806_10241_gb300.serving import Server
+    monkeypatch.setattr(autotune, "_CACHE", str(tmp_path / "autotune.json"))
+    reqs = _stream(5)
+    kw = dict(steps_per_round=100, check_every=200, window=400, tol=1e-7, max_steps=1400)
+    srv = Server(storage="fp32", keep_results=True, autotune=True, **kw)
+    rep = srv.run(reqs)
+    assert (tmp_path / "autotune.json").exists()  # the candidates were timed
+    seq = Server(storage="fp32", **kw).run_sequential(reqs, storage="fp32")
+    got = {r.rid: r for r in rep.records}
+    for r in seq.records:
+        assert (got[r.rid].status, got[r.rid].steps) == (r.status, r.steps), r.rid
+        assert got[r.rid].nu == r.nu, r.rid
+        want = _alone(reqs[r.rid], r.steps, "fp32", 100)
+        assert np.array_equal(srv.results[r.rid], want), r.rid
