@@ -97,3 +97,20 @@ def test_cached_persistent_batch_launch_is_rechecked(tmp_path, monkeypatch):
     too_many = FakeBatch(resident=100, items=150)
     best = autotune.tune_batch(too_many)
     assert timed and best[2] != 5  # tuned again, and no persistent candidate could run
+
+
+def test_has_cached_batch_launch(tmp_path, monkeypatch):
+    """The server asks whether a batch's launch is cached (then it takes no
+    tuning steps): not without an entry, yes for a cached launch, and not
+    for a cached persistent launch whose items are not all resident."""
+    path = tmp_path / "autotune.json"
+    monkeypatch.setattr(autotune, "_CACHE", str(path))
+    b = FakeBatch(resident=100, items=50)
+    assert not autotune.has_cached_batch_launch(b)
+    key = f"batch/fp32/{autotune._size_class(4096)}/{autotune._size_class(1)}"
+    path.write_text(json.dumps({key: {"launch": [4, 2, 4], "waves": 1.0, "ms_per_step": 0.01}}))
+    assert autotune.has_cached_batch_launch(b) and b.launches[-1][:2] == (4, 2)
+    path.write_text(json.dumps({key: {"launch": [4, 2, 5], "waves": 1.0, "ms_per_step": 0.01}}))
+    assert autotune.has_cached_batch_launch(b)
+    assert not autotune.has_cached_batch_launch(FakeBatch(resident=100, items=150))
+    assert b.steps == 0
