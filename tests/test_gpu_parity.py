@@ -242,8 +242,7 @@ def test_fields_after_1000_steps_every_family(name, storage, tol):
         assert dg["nu_avg"] == pytest.approx(do["nu_avg"], rel=1e-4 if storage == "fp32" else 1e-10)
 
 
-@pytest.mark.parametrize("name", ["annulus_walls", "cylinder_axis", "periodic_annulus", "czochralski",
-                                  "free_ends_annulus"])
+@pytest.mark.parametrize("name", list(BUILDERS))
 def test_fp64_fields_and_diagnostics_match_oracle(name):
     params = BUILDERS[name](45, 38)
     st = random_state(params, seed=11)
