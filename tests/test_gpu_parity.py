@@ -418,10 +418,13 @@ def test_far_corner_of_a_lattice_beyond_4_gib_matches_a_small_copy():
 
 @pytest.mark.parametrize("storage,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
 def test_stream_function_matches_oracle(storage, tol):
-    """Stream function (Sec. 3.6) of a heated swirling cylinder and of an
-    annulus (inner boundary: the axis, an inner wall) after 300 steps."""
+    """Stream function (Sec. 3.6) of a heated swirling cylinder, of an
+    annulus (inner boundary: the axis, an inner wall) and of the Czochralski
+    melt (split top with a free surface; the quantity of Table 4) after 300
+    steps."""
     for c in (W.swirling_cylinder(nr=70, nz=96, Re=200.0, Ra=1e5, amp=1e-3, seed=3),
-              W.annulus_convection(nr=45, nz=61, Ra=1e5, amp=1e-3, seed=4, swirl_inner=0.01)):
+              W.annulus_convection(nr=45, nz=61, Ra=1e5, amp=1e-3, seed=4, swirl_inner=0.01),
+              W.czochralski(nr=50, nz=50, beta=0.4, Re_x=200.0, Re_c=-50.0, Pr=0.7, Gr=1e4)):
         g = Solver(c.params, storage=storage)
         g.init_fields(c.fields)
         g.step(300)
