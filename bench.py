@@ -266,12 +266,15 @@ def run_serving(args):
 
 
 def batch_measure(instances, lo, hi, storage, steps, warmup, graph_steps, oracle_instances, repeats=1,
-                  clocks=None):
-    """Uneven annulus-convection lattices (nr, nz ~ U{lo..hi}, seeds
-    0..instances-1) advanced together by the batched step, replayed from CUDA
-    graphs, the launch autotuned per batch: median aggregate MLUPS over
+                  clocks=None, kind="annuli"):
+    """Uneven lattices advanced together by the batched step, replayed from
+    CUDA graphs, the launch autotuned per batch: median aggregate MLUPS over
     `repeats` timed regions of `steps` steps, the HBM roofline, and the Nu of
-    the smallest instances against the oracle after the same steps."""
+    the smallest instances against the oracle after the same steps.  kind
+    "annuli": annulus-convection lattices, nr, nz ~ U{lo..hi}, seeds
+    0..instances-1; "requests": the lattices of the serving stream's first
+    `instances` requests with nr ~ U{lo..hi} (60 % annuli, 40 % swirling
+    cylinders, nz = nr U{1,2})."""
     import numpy as np
     import torch
     import oracle
@@ -279,7 +282,14 @@ def batch_measure(instances, lo, hi, storage, steps, warmup, graph_steps, oracle
     from paper_1806_10241_gb300 import workloads as W
     from paper_1806_10241_gb300.batch import Batch
     from paper_1806_10241_gb300.solver import Solver
-    cases = W.batched_instances(instances, lo=lo, hi=hi)
+    if kind == "requests":
+        cases = [r.case for r in W.serving_requests(count=instances, rate=50.0, seed=0, nr_lo=lo, nr_hi=hi)]
+        desc = (f"{len(cases)} lattices of the serving stream (seed 0): nr ~ U{{{lo}..{hi}}}, nz = nr U{{1,2}}, "
+                "60 % annulus convection, 40 % swirling cylinder")
+    else:
+        cases = W.batched_instances(instances, lo=lo, hi=hi)
+        desc = (f"{len(cases)} annulus-convection lattices, nr, nz ~ U{{{lo}..{hi}}}, "
+                "R_o/R_i ~ U[1.5,3], Ra log-U[1e3,1e5], inner swirl ~ U[0,0.05], seeds 0..")
     stream = torch.cuda.Stream()
     solvers = []
     for cs in cases:
@@ -328,8 +338,7 @@ def batch_measure(instances, lo, hi, storage, steps, warmup, graph_steps, oracle
     return {"value": round(nodes * steps / (med * 1e3), 1), "unit": "MLUPS", "steps": steps, "warmup": warmup,
             "repeats": repeats, "ms_per_step": round(med / steps, 5),
             "mlups_range": [round(nodes * steps / (max(ms) * 1e3), 1), round(nodes * steps / (min(ms) * 1e3), 1)],
-            "config": {"workload": f"{len(cases)} annulus-convection lattices, nr, nz ~ U{{{lo}..{hi}}}, "
-                                   "R_o/R_i ~ U[1.5,3], Ra log-U[1e3,1e5], inner swirl ~ U[0,0.05], seeds 0..",
+            "config": {"workload": desc,
                        "nodes": nodes, "storage": storage,
                        "launch": {"seg_rows": launch[0], "warps_per_block": launch[1], "row_fetch": launch[2],
                                   "graph_steps": graph_steps,
@@ -354,7 +363,7 @@ def run_batch(args):
     torch.cuda.set_device(0)
     m = batch_measure(args.instances, args.batch_lo, args.batch_hi, args.batch_storage, args.steps, args.warmup,
                       args.graph_steps, args.oracle_instances, repeats=max(1, args.repeats),
-                      clocks=ClockSampler(0))
+                      clocks=ClockSampler(0), kind=args.batch_set)
     line = {"metric": METRIC, "value": m["value"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": m["dtype"], "data": "synthetic",
@@ -564,6 +573,8 @@ def main():
     ap.add_argument("--workload", default="cylinder", choices=["cylinder", "serving", "precision", "batch"])
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--batch-storage", dest="batch_storage", default="fp16", choices=["fp16", "bf16", "fp32"])
+    ap.add_argument("--batch-set", dest="batch_set", default="annuli", choices=["annuli", "requests"],
+                    help="batch of uneven annuli, or the lattices of the serving stream's first requests")
     ap.add_argument("--batch-lo", dest="batch_lo", type=int, default=32)
     ap.add_argument("--batch-hi", dest="batch_hi", type=int, default=512)
     ap.add_argument("--graph-steps", dest="graph_steps", type=int, default=50)
