@@ -13,7 +13,9 @@ replayed from a CUDA graph).  Between rounds it
   * evaluates the diagnostics of each active lattice every `check_every`
     steps and retires the ones that reached the steady state
     (|Nu(t) - Nu(t - window)| < tol), hit the step cap or diverged,
-  * rebuilds the batch when its membership changed.
+  * rebuilds the batch when its membership changed (with autotune, a new
+    size class is tuned on scratch copies of the lattices, so that the
+    live ones are checked at the same steps as in a solo run).
 A request whose lattice can never fit the budget is rejected; `cancel(rid)`
 withdraws a request (pending: dropped; active: retired at the end of the
 round).  Latency of a request = finish time - arrival time.
