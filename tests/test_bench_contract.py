@@ -68,3 +68,22 @@ def test_gpu_arm_line_carries_the_16bit_batch_and_serving_results():
     sv = line["serving"]
     assert sv["solves_per_s"] > 0 and sv["p99_latency_s"] >= sv["p50_latency_s"] > 0
     assert sv["sequential_fp32"]["solves_per_s"] > 0
+
+
+def test_committed_counters_are_used_only_for_the_sources_they_were_taken_on(tmp_path, monkeypatch):
+    """The roofline's `traffic` and the issue roofline's instruction count come
+    from the committed ncu summary only while its hash matches the step
+    kernels' sources and nvcc flags."""
+    sys.path.insert(0, ROOT)
+    import bench
+    p = tmp_path / "counters.json"
+    key = "k_step3_tma_fp32_1024x2048"
+    monkeypatch.setattr(bench, "PROFILE_JSON", str(p))
+    p.write_text(json.dumps({key: {"kernel_source_sha256_16": bench.kernel_source_hash(),
+                                   "dram_bytes_per_launch": 123, "warp_instructions_per_launch": 456}}))
+    assert bench.counters_for(key) == 123
+    assert bench.counters_for(key, "warp_instructions_per_launch") == 456
+    p.write_text(json.dumps({key: {"kernel_source_sha256_16": "0" * 16, "dram_bytes_per_launch": 123}}))
+    assert bench.counters_for(key) is None
+    assert bench.counters_for("no_such_kernel") is None
+
