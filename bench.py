@@ -678,17 +678,20 @@ def main():
     host_out = torch.empty((5, case.nz, case.nr), dtype=torch.float64).pin_memory()
     ge = Solver(case.params, storage=args.storage, device=dev)
     e_steps = 2000
-    barrier()
-    t = time.perf_counter()
-    ge.init_fields(host_in.numpy())
-    ge.step(e_steps)
-    ge.fields(out=host_out.numpy())
-    barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t, dist, dev)
+    e_times = []
+    for _ in range(3):  # three solves, the median reported (host-side timing varies)
+        barrier()
+        t = time.perf_counter()
+        ge.init_fields(host_in.numpy())
+        ge.step(e_steps)
+        ge.fields(out=host_out.numpy())
+        barrier()
+        e_times.append(max_over_ranks(time.perf_counter() - t, dist, dev))
+    e2e_s = sorted(e_times)[1]
     e2e = {"value": round(world * nodes * e_steps / e2e_s / 1e6, 1), "unit": "MLUPS",
            "h2d_bytes_per_step": int(host_in.numel() * 8 / e_steps),
            "d2h_bytes_per_step": int(host_out.numel() * 8 / e_steps),
-           "steps": e_steps,
+           "steps": e_steps, "solves": len(e_times), "statistic": "median solve",
            "what": "one solve: lb_init_fields (pinned host fields) + 2000 lb_step + lb_get_fields to host"}
     del ge
 
