@@ -178,7 +178,7 @@ def test_autotuned_server_stops_every_request_where_a_solo_run_does(tmp_path, mo
     """With an empty autotuner cache the server times the launch candidates on
     scratch copies of the active lattices, so the live ones take no extra
     steps: every request is checked at the same steps as in a sequential solo
-    run, reaches the same verdict at the same step, and ends in the same bits."""
+    run, reaches the same outcome at the same step, and ends in the same bits."""
     from paper_1806_10241_gb300 import autotune
     from paper_1806_10241_gb300.serving import Server
     monkeypatch.setattr(autotune, "_CACHE", str(tmp_path / "autotune.json"))
